@@ -1,0 +1,392 @@
+"""Benchmark of the black-hole beam tracer on GB300.
+
+A step renders one 1920x1080 frame of the orbiting-camera workload (camera
+at r = 6 r_s, theta = 85 deg, moving at 0.5 c along e_phi; thin disc 3-12 r_s;
+1M synthetic stars in a 6 x 2048^2 FP16 cube map; 512x512 and 64x32 FP32
+tables) through the C ABI.  Tables and cube map are built once, untimed
+(their build times are reported separately).  L2 is flushed (a 256 MiB
+write) before every timed frame; each frame's render is timed with CUDA
+events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: replicas only -- every rank renders its own frames, no collective
+on the data path; value = frames of all ranks / max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "1080p frames/s"
+WORKLOAD = "orbit_1080p"
+# FP32 work per unit, counted from the render kernel source (FMA = 2 flops):
+# beam set-up + TRACERAY + footprint + colour lookup + store per pixel, the
+# tent-filter inner loop per visited texel, disc shading per hit.
+FLOP_PER_PIXEL = 420
+FLOP_PER_TEXEL = 26
+FLOP_PER_HIT = 60
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                mhz.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return None
+
+
+def render_traffic():
+    """DRAM bytes per render launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    f = ROOT / "profiles" / "render_traffic.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text())
+    src = (ROOT / "paper_2010_08735_gb300" / "csrc" / "bh_render.cu").read_bytes()
+    if d.get("kernel_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def orbit_camera(wk, step):
+    cam = dict(wk["camera"])
+    cam["phi"] = cam["phi"] + 0.002 * step  # the camera moves along its orbit between frames
+    return cam
+
+
+def cpu_baseline(wk, seconds=12.0, impl_line=False):
+    """The oracle, as it stands, on the host cores: full-resolution rows of the
+    same workload until about `seconds` of rendering, scaled to frames/s."""
+    import oracle
+    from paper_2010_08735_gb300 import synth
+    t0 = time.perf_counter()
+    D, U = oracle.tables_exact(512, 64, 32, 1e-3)
+    Ct, dl = oracle.colour_table(), oracle.disc_colour_table()
+    st = synth.stars(wk["n_stars"], wk["star_seed"])
+    rec = oracle.build_cubemap(st, wk["cube_n"], 1 if wk["cube_dtype"] == "f16" else 2)
+    scene = oracle.SceneTables(D.astype(np.float32), U.astype(np.float32), Ct.astype(np.float32),
+                               dl.astype(np.float32), rec, wk["cube_n"],
+                               1 if wk["cube_dtype"] == "f16" else 2)
+    setup = time.perf_counter() - t0
+    cam = wk["camera"]
+    H = cam["height"]
+    cores = os.cpu_count() or 1
+    rows, tr = 0, 0.0
+    band = 40
+    y = (H // 2 - 200) // 2 * 2
+    while tr < seconds and rows < H:
+        y0 = y % H
+        y0 -= y0 % 2
+        y1 = min(y0 + band, H)
+        t = time.perf_counter()
+        oracle.render(cam, wk["disc"], scene, exposure_stars=0.01, y0=y0, y1=y1, nthreads=cores)
+        tr += time.perf_counter() - t
+        rows += y1 - y0
+        y += band
+    fps = (rows / H) / tr
+    return {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows} of {H} rows of the 1920x1080 frame ({rows * cam['width']} px), "
+                      f"FP64 C oracle with {cores} threads; oracle set-up {setup:.1f} s untimed"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2010_08735_gb300 import synth
+    wk = synth.WORKLOADS[WORKLOAD]
+    cb = cpu_baseline(wk, seconds=max(5.0, 2.0 * args.steps), impl_line=True)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "frames/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": 1920, "height": 1080, "stars": wk["n_stars"],
+                       "cube_face": wk["cube_n"], "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_08735_gb300 import bh, synth
+
+    wk = synth.WORKLOADS[WORKLOAD]
+    cam0 = wk["camera"]
+    W, H = cam0["width"], cam0["height"]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = bh.bh_create(local, 0)
+    sh = bh.make_shading(1.0, 0.01)
+    disc = wk["disc"]
+    # --- build (untimed for the frame metric; reported)
+    t_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        t_ev[0].record(stream)
+        tables = bh.bh_precompute_tables(ctx, 512, 64, 32, bh.BH_F32, stream)
+        t_ev[1].record(stream)
+        stars = torch.from_numpy(synth.stars(wk["n_stars"], wk["star_seed"])).to(dev)
+        t_ev[2].record(stream)
+        cube = bh.bh_build_star_cubemap(ctx, stars, wk["cube_n"],
+                                        bh.BH_F16 if wk["cube_dtype"] == "f16" else bh.BH_BF16, stream)
+        t_ev[3].record(stream)
+    stream.synchronize()
+    precompute_ms = t_ev[0].elapsed_time(t_ev[1])
+    cubemap_ms = t_ev[2].elapsed_time(t_ev[3])
+
+    out = torch.empty((H, W, 4), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # --- work counts for the roofline (one untimed debug render)
+    dbg = torch.empty((H, W, 16), device=dev)
+    bh.bh_render_debug(ctx, tables, cube, cam0, disc, sh, out, dbg, stream)
+    stream.synchronize()
+    d = dbg.view(-1, 16)
+    texels = float(d[:, 15].sum().item())
+    hits = float(d[:, 3].sum().item())
+    del dbg, d
+    flops_frame = W * H * FLOP_PER_PIXEL + texels * FLOP_PER_TEXEL + hits * FLOP_PER_HIT
+
+    # --- warm-up
+    for s in range(args.warmup):
+        bh.bh_render(ctx, tables, cube, orbit_camera(wk, s), disc, sh, out, stream)
+    stream.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = bh.bh_kernel_launches(ctx)
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()  # L2 flush between timed frames (256 MiB > 129 MB L2)
+            evs[s][0].record(stream)
+            bh.bh_render(ctx, tables, cube, orbit_camera(wk, args.warmup + s), disc, sh, out, stream)
+            evs[s][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clocks = sampler.stop()
+    launches = bh.bh_kernel_launches(ctx) - launches0
+    frame_ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(frame_ms) / 1000.0
+    if ws > 1:
+        tt = torch.tensor([t_dev], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    ms_per_step = 1000.0 * t_dev / args.steps
+    fps = ws * args.steps / t_dev
+
+    # --- end to end through the C ABI with host buffers (D2H of every frame)
+    host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    for s in range(2):
+        bh.bh_render_to_host(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
+    e2e_steps = max(5, args.steps // 2)
+    t = time.perf_counter()
+    for s in range(e2e_steps):
+        bh.bh_render_to_host(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
+    e2e_t = time.perf_counter() - t
+    e2e_fps = ws * e2e_steps / e2e_t
+
+    # --- served (continuous batching) and batched forms on the same frames
+    served = serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=max(32, args.steps))
+    batched = batch_run(bh, ctx, tables, cube, sh, dev)
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clocks or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops_frame / (ms_per_step / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": W, "height": H, "camera": "r=6, theta=85deg, v=0.5c e_phi",
+                   "stars": wk["n_stars"], "cube_face": wk["cube_n"], "cube_dtype": wk["cube_dtype"],
+                   "tables": "512x512 D + 64x32 U, FP32", "l2": "flushed (256 MiB write) before each frame",
+                   "parallelism": f"replicas x{ws}"},
+        "mpix_per_s": fps * W * H / 1e6,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": render_traffic(),
+                     "peak_note": f"FP32 issue: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
+                     "flops_per_frame": flops_frame, "texels_per_pixel": texels / (W * H)},
+        "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 200,
+                "d2h_bytes_per_step": W * H * 16},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+        "precompute_ms": {"tables_D_U_colour": precompute_ms, "cubemap_1M_stars": cubemap_ms},
+        "served": served, "batched": batched,
+    }
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wk, seconds=12.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    bh.bh_cubemap_free(cube)
+    bh.bh_tables_free(tables)
+    bh.bh_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=64, viewers=16):
+    """Serve `frames` 1080p frame requests from `viewers` viewers as fast as they
+    complete (each viewer resubmits when its frame is done)."""
+    import torch
+    cam0 = wk["camera"]
+    W, H = cam0["width"], cam0["height"]
+    outs = [torch.empty((H, W, 4), device=dev) for _ in range(viewers)]
+    pending = {}
+    lat = []
+    submitted = done = 0
+    t0 = time.perf_counter()
+    while done < frames:
+        for v in range(viewers):
+            if v not in pending and submitted < frames:
+                cam = orbit_camera(wk, submitted)
+                st, tk = bh.bh_serve_submit(ctx, tables, cube, v, cam, wk["disc"], sh, outs[v])
+                if st == bh.BH_OK:
+                    pending[v] = tk
+                    submitted += 1
+        for v, tk in list(pending.items()):
+            st, ms = bh.bh_serve_poll(ctx, tk, 0)
+            if st == bh.BH_OK:
+                lat.append(ms)
+                done += 1
+                del pending[v]
+        time.sleep(0)
+    el = time.perf_counter() - t0
+    lat.sort()
+    return {"frames_per_s": frames / el, "unit": "1080p frames/s", "viewers": viewers,
+            "frames": frames, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+
+def batch_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
+    """64 cameras of mixed resolution in one persistent launch; Mpix/s and
+    1080p-equivalent frames/s, after the autotuner picked a tile shape."""
+    import torch
+    from paper_2010_08735_gb300 import synth
+    cams = synth.batch_cameras(n, seed=1)
+    outs = [torch.empty((c["height"], c["width"], 4), device=dev) for c in cams]
+    disc = synth.disc()
+    chosen = bh.bh_autotune_batch(ctx, tables, cube, cams, disc, sh, outs)
+    s = torch.cuda.Stream(device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bh.bh_render_batch(ctx, tables, cube, cams, disc, sh, outs, s)
+    s.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        bh.bh_render_batch(ctx, tables, cube, cams, disc, sh, outs, s)
+    e1.record(s)
+    s.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    px = sum(c["width"] * c["height"] for c in cams)
+    return {"cameras": n, "mpix_per_batch": px / 1e6, "ms_per_batch": ms,
+            "mpix_per_s": px / 1e6 / (ms / 1000.0), "frames_1080p_equiv_per_s": px / (1920 * 1080) / (ms / 1000.0),
+            "autotune_choice": chosen}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

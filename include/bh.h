@@ -1,0 +1,238 @@
+/*
+ * bh.h -- C ABI of libbh, a GB300 (sm_103a) implementation of the
+ * table-driven beam tracer for a non-rotating (Schwarzschild) black hole of
+ * E. Bruneton, "Real-time High-Quality Rendering of Non-Rotating Black
+ * Holes" (2020).
+ *
+ * The problem statement (Sec. 3, Sec. 4): camera position, velocity and
+ * orientation, accretion-disc parameters and a star list in; a linear-RGB
+ * image out.  Units: horizon radius r_s = 1 and c = 1 (Sec. 3.1).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a bh_status; no exception or signal crosses the ABI.
+ *    On failure bh_last_error() returns a message for the calling thread.
+ *  - Handles (bh_ctx, bh_tables, bh_cubemap) are owned by the library and
+ *    released by their _free / bh_destroy call.  Image buffers are owned by
+ *    the caller.
+ *  - "device" pointers are CUDA device pointers of the context's device;
+ *    "host" pointers are ordinary (preferably pinned) host memory.
+ *  - Streams are passed as void* holding a cudaStream_t (NULL = the legacy
+ *    default stream).  Calls that take a stream only enqueue work on it
+ *    unless their comment says they synchronise.
+ *  - Invalid physics is rejected with BH_ERR_INVALID_ARG: camera radius
+ *    r <= 1 (no static observer inside the horizon, Sec. 5), |v| >= 1, a
+ *    non-orthonormal orientation, disc r_in < 3 (innermost stable circular
+ *    orbit, Sec. 3.3.3) or r_out <= r_in.
+ */
+#ifndef BH_H
+#define BH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BH_OK = 0,
+  BH_ERR_INVALID_ARG = 1,   /* a pointer, size or physical parameter is out of range */
+  BH_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
+  BH_ERR_OOM = 3,           /* device allocation failed or the memory budget is exceeded */
+  BH_ERR_BUSY = 4,          /* serving: admission refused the request */
+  BH_ERR_NOT_READY = 5,     /* serving: the ticket's frame is not finished yet */
+  BH_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  BH_ERR_DEVICE_STATUS = 7  /* a kernel reported an error through its status word */
+} bh_status;
+
+typedef enum { BH_F32 = 0, BH_F16 = 1, BH_BF16 = 2 } bh_dtype;
+
+typedef struct bh_ctx bh_ctx;
+typedef struct bh_tables bh_tables;
+typedef struct bh_cubemap bh_cubemap;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the serving loop may hold for frames in flight (0 = no
+ * bound).  The context owns a status word, small staging buffers and, once
+ * used, the serving streams. */
+bh_status bh_create(int device, size_t hbm_budget_bytes, bh_ctx **out);
+void bh_destroy(bh_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until
+ * the next call on this thread. */
+const char *bh_last_error(void);
+
+/* Number of kernel launches the context has issued so far (all entry
+ * points), for launch accounting. */
+long long bh_kernel_launches(const bh_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Tables D(e,u), U(e,phi) (Algorithm 1 PRECOMPUTE, Sec. 3.3.2-3.3.3,        */
+/* Appendix A) and the colour tables (Sec. 3.4.2)                             */
+/* ------------------------------------------------------------------------ */
+
+/* d_n x d_n deflection table D (d_n even, 4..4096; the paper uses 512) and
+ * u_ne x u_nphi disc table U (the paper uses 64 x 32; u_ne * u_nphi <= 4096).
+ * storage: BH_F32 or BH_F16 for the copies the renderer reads.  Texel i of n
+ * holds the Appendix A coordinate i/(n-1). */
+typedef struct {
+  int d_n;
+  int u_ne;
+  int u_nphi;
+  bh_dtype storage;
+} bh_table_desc;
+
+/* Compute D and U on the GPU by FP64 quadrature of the ray equation
+ * (Eq. rayequation: (du/dphi)^2 = e^2 - u^2 (1-u)), one thread per texel, and
+ * the colour tables: C(xy, D) (64 x 32 x 64, Sec. 3.4.2) and the black-body
+ * table used for the disc.  Enqueued on `stream`; *out is usable by later
+ * work on the same stream at once.  Allocates device memory (~10 MiB). */
+bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc, void *stream,
+                               bh_tables **out);
+
+/* Same handle from host FP64 values (D[j*d_n + i], U[j*u_ne + i]; i indexes
+ * e, j indexes u or phi), converted to the storage type on the device; the
+ * colour tables are computed on the GPU as in bh_precompute_tables.
+ * Synchronises `stream`. */
+bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, const double *D_host,
+                           const double *U_host, void *stream, bh_tables **out);
+
+/* Copy the FP64 values of D and U to host buffers (d_n*d_n and
+ * u_ne*u_nphi doubles; either may be NULL).  Synchronises the context's
+ * device. */
+bh_status bh_tables_copy_out(const bh_tables *t, double *D_host, double *U_host);
+
+/* Copy the colour tables: C as [log2 D][y][x] float4 (XYZ, pad), 64*32*64*4
+ * floats; the disc table as 1024 float4 (ln X, ln Y, ln Z, pad).  Either may
+ * be NULL.  Synchronises. */
+bh_status bh_tables_copy_colour(const bh_tables *t, float *C_host, float *disc_host);
+void bh_tables_free(bh_tables *t);
+
+/* ------------------------------------------------------------------------ */
+/* Star cube map (Sec. 3.3.2 "Emitted light", Sec. 4)                         */
+/* ------------------------------------------------------------------------ */
+
+/* A synthetic star: unit direction in the black hole's Cartesian frame,
+ * luminosity (X+Y+Z of its emitted colour) and black-body temperature. */
+typedef struct {
+  float dir[3];
+  float lum;
+  float temp_K;
+} bh_star;
+
+/* Bin n stars into a 6 x face_size^2 cube map with a full mip chain: each
+ * texel stores the colour sum (X, Y, Z as half or bfloat16 of the sum
+ * divided by 4^level) and the luminance-weighted mean star position inside
+ * the texel (two unorm8); mips sum colours and average positions weighted by
+ * Y.  face_size: power of two, 1..8192.  storage: BH_F16 or BH_BF16.
+ * stars: host array (stars_on_device = 0) or device array (1).  Enqueued on
+ * `stream` (a host star list is staged synchronously first).  Uses
+ * 40 * 6 * face_size^2 bytes of scratch, freed before return. */
+bh_status bh_build_star_cubemap(bh_ctx *ctx, const bh_star *stars, long long n, int face_size,
+                                bh_dtype storage, int stars_on_device, void *stream,
+                                bh_cubemap **out);
+
+/* Number of texel records (all faces, all levels) of a cube map. */
+long long bh_cubemap_records(int face_size);
+
+/* Copy all records (4 uint16 per texel, level-major, face, row, column) to
+ * the host; n_records must equal bh_cubemap_records(face_size).  Synchronises. */
+bh_status bh_cubemap_copy_out(const bh_cubemap *c, uint16_t *records_host, long long n_records);
+void bh_cubemap_free(bh_cubemap *c);
+
+/* ------------------------------------------------------------------------ */
+/* Rendering (Sec. 3.2-3.4, Algorithm 1 TRACERAY)                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double r, theta, phi; /* Schwarzschild position, r > 1 */
+  double v[3];          /* velocity wrt the static observer, components on (e_r, e_theta, e_phi), |v| < 1 */
+  double orient[9];     /* O, row-major: rows e_w, e_h, e_d on the boosted (r', theta', phi') axes */
+  double fov_y;         /* vertical field of view, radians, in (0, pi) */
+  int width, height;    /* pixels, 1..16384 each */
+} bh_camera;
+
+typedef struct {
+  double r_in, r_out; /* 3 <= r_in < r_out; disc in the z = 0 plane, prograde about +z */
+  double t_peak_K;    /* temperature at r = 49/12, where T^4 ~ u^3 (1 - sqrt(3u)) peaks */
+  double density;     /* in [0,1]: emission weight and opacity of each disc crossing */
+  int enabled;
+} bh_disc;
+
+typedef struct {
+  float exposure_disc;  /* disc radiance scale: 1 = peak black body of Y = 1 */
+  float exposure_stars; /* star radiance scale */
+} bh_shading;
+
+/* Render one frame: out_rgba_device holds width*height float4 (linear sRGB,
+ * A = 1), row-major, top row first; caller-owned device memory, 16-byte
+ * aligned.  cubemap may be NULL (no stars).  Enqueued on `stream`. */
+bh_status bh_render(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                    const bh_camera *camera, const bh_disc *disc, const bh_shading *shading,
+                    float *out_rgba_device, void *stream);
+
+/* As bh_render, plus 16 floats per pixel of intermediate values in
+ * dbg_device: e^2, delta, delta' (+inf if captured), number of disc hits,
+ * u0, u1, mip level (-1: no star term), cube face, Omega/Omega', star
+ * Doppler factor, gathered star X, Y, Z, hit-0 Doppler, hit-1 Doppler,
+ * texels visited. */
+bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                          const bh_camera *camera, const bh_disc *disc,
+                          const bh_shading *shading, float *out_rgba_device, float *dbg_device,
+                          void *stream);
+
+/* End-to-end form: render into a context-owned device frame buffer and copy
+ * the image to out_rgba_host (width*height*4 floats; pinned memory gives the
+ * fastest copy).  Synchronises `stream` before returning. */
+bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                            const bh_camera *camera, const bh_disc *disc,
+                            const bh_shading *shading, float *out_rgba_host, void *stream);
+
+/* Render n cameras of any sizes in one persistent launch driven by a tile
+ * queue: outs[k] is camera k's device image (as bh_render).  The per-camera
+ * constants are staged through the context.  Enqueued on `stream`. */
+bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap, int n,
+                          const bh_camera *cameras, const bh_disc *disc,
+                          const bh_shading *shading, float *const *outs, void *stream);
+
+/* Autotuning of the batched launch: time the candidate tile shapes on the
+ * given cameras (renders them several times, synchronously) and keep the
+ * fastest for later bh_render_batch calls of this context.  *chosen receives
+ * the chosen candidate index (may be NULL). */
+bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                            int n, const bh_camera *cameras, const bh_disc *disc,
+                            const bh_shading *shading, float *const *outs, int *chosen);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of frame requests from many viewers          */
+/* ------------------------------------------------------------------------ */
+
+/* Submit a frame request of viewer `viewer` (0..65535) into a caller-owned
+ * device buffer.  Requests are batched with those already queued and start
+ * as soon as a launch slot frees; admission is refused with BH_ERR_BUSY if
+ * the frame does not fit the context's memory budget or the viewer already
+ * has a frame queued (reading: at most one queued and one in flight per
+ * viewer).  *ticket identifies the request for bh_serve_poll. */
+bh_status bh_serve_submit(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                          int viewer, const bh_camera *camera, const bh_disc *disc,
+                          const bh_shading *shading, float *out_rgba_device,
+                          unsigned long long *ticket);
+
+/* Progress the serving loop and report on a ticket: BH_OK when its frame is
+ * finished (latency_ms = submit to completion), BH_ERR_NOT_READY while
+ * pending (waits up to timeout_us microseconds first; 0 = do not wait). */
+bh_status bh_serve_poll(bh_ctx *ctx, unsigned long long ticket, int timeout_us,
+                        double *latency_ms);
+
+/* Launch whatever is queued without waiting for more requests. */
+bh_status bh_serve_flush(bh_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BH_H */

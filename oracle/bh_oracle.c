@@ -921,7 +921,7 @@ double orc_disc_temperature(double t_peak, double u) {
 /* Per-pixel render                                                          */
 /* ------------------------------------------------------------------------ */
 
-#define NDBG 16
+#define NDBG 20
 typedef struct {
   const orc_camera *cam;
   const orc_disc *disc;
@@ -1001,7 +1001,6 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
     case 4: dmaw = dw[2]; dmah = dh[2]; dscw = dw[0]; dsch = dh[0]; dtcw = -dw[1]; dtch = -dh[1]; break;
     default: dmaw = -dw[2]; dmah = -dh[2]; dscw = -dw[0]; dsch = -dh[0]; dtcw = -dw[1]; dtch = -dh[1]; break;
   }
-  (void)d;
   int N = sc->cube_n;
   double hN = 0.5 * N;
   double S = (sc_ / ma + 1.0) * hN, T = (tc_ / ma + 1.0) * hN;
@@ -1011,6 +1010,15 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
   double hs = fabs(Jsw) + fabs(Jsh), ht = fabs(Jtw) + fabs(Jth);
   double hm = hs > ht ? hs : ht;
   int nl = orc_cube_levels(N);
+  {
+    /* decision margins, for masking comparisons at discontinuities */
+    double a[3] = {fabs(d[0]), fabs(d[1]), fabs(d[2])}, mx = a[0], sd = -1.0;
+    for (int k = 1; k < 3; ++k) if (a[k] > mx) mx = a[k];
+    for (int k = 0; k < 3; ++k) if (a[k] < mx && a[k] > sd) sd = a[k];
+    int nmax = (a[0] == mx) + (a[1] == mx) + (a[2] == mx);
+    dbg[16] = hm;
+    dbg[17] = nmax > 1 ? 0.0 : 1.0 - sd / mx;
+  }
   int L = 0;
   if (J->force_level >= 0) L = J->force_level;
   else
@@ -1022,6 +1030,7 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
   double a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
   double det = a11 * a22 - a12 * a21;
   /* reading C18: skip a degenerate footprint */
+  dbg[18] = fabs(det) / sqrt((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22));
   if (!(fabs(det) > 1e-6 * sqrt((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22)))) return;
   double i11 = a22 / det, i12 = -a12 / det, i21 = -a21 / det, i22 = a11 / det;
   int i0 = (int)floor(cS - hsL), i1 = (int)floor(cS + hsL);
@@ -1145,7 +1154,8 @@ static void *render_worker(void *argp) {
  *  0 e^2, 1 delta, 2 delta' (inf if captured), 3 hits, 4 u0, 5 u1,
  *  6 mip level (-1: no star term), 7 face, 8 Omega/Omega', 9 star Doppler,
  *  10..12 gathered star XYZ, 13 hit-0 Doppler, 14 hit-1 Doppler,
- *  15 texels visited.
+ *  15 texels visited, 16 footprint half extent (level-0 texels),
+ *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|).
  * force_level >= 0 forces the mip level (for the flat-space checks). */
 int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc,
                double exposure_stars, const orc_scene *sc, int y0, int y1, int force_level,

@@ -1,0 +1,345 @@
+"""Python binding of libbh (ctypes), one function per C-ABI entry point.
+
+Argument marshalling only: every step of the render and of the precompute
+runs in the CUDA kernels of ``libbh.so``.  Device buffers are passed as raw
+device pointers (``int``) or as torch CUDA tensors; streams as
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers or ``None``.
+There is no CPU fallback: if ``libbh.so`` is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+LIBPATH = HERE / "libbh.so"
+
+BH_OK, BH_ERR_INVALID_ARG, BH_ERR_CUDA, BH_ERR_OOM, BH_ERR_BUSY, BH_ERR_NOT_READY, \
+    BH_ERR_TIMEOUT, BH_ERR_DEVICE_STATUS = range(8)
+BH_F32, BH_F16, BH_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "BH_OK", 1: "BH_ERR_INVALID_ARG", 2: "BH_ERR_CUDA", 3: "BH_ERR_OOM",
+                4: "BH_ERR_BUSY", 5: "BH_ERR_NOT_READY", 6: "BH_ERR_TIMEOUT",
+                7: "BH_ERR_DEVICE_STATUS"}
+NDBG = 16
+
+
+class BhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Camera(C.Structure):
+    _fields_ = [("r", C.c_double), ("theta", C.c_double), ("phi", C.c_double),
+                ("v", C.c_double * 3), ("orient", C.c_double * 9), ("fov_y", C.c_double),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class Disc(C.Structure):
+    _fields_ = [("r_in", C.c_double), ("r_out", C.c_double), ("t_peak_K", C.c_double),
+                ("density", C.c_double), ("enabled", C.c_int)]
+
+
+class Shading(C.Structure):
+    _fields_ = [("exposure_disc", C.c_float), ("exposure_stars", C.c_float)]
+
+
+class TableDesc(C.Structure):
+    _fields_ = [("d_n", C.c_int), ("u_ne", C.c_int), ("u_nphi", C.c_int), ("storage", C.c_int)]
+
+
+class Star(C.Structure):
+    _fields_ = [("dir", C.c_float * 3), ("lum", C.c_float), ("temp_K", C.c_float)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libbh.so (built by ``__graft_entry__.build()`` or ``build.py``)."""
+    global _lib
+    if _lib is None:
+        if not LIBPATH.exists():
+            raise BhError(BH_ERR_CUDA, f"{LIBPATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(str(LIBPATH))
+        P = C.POINTER
+        sig = {
+            "bh_create": [C.c_int, C.c_size_t, P(_vp)],
+            "bh_destroy": None,
+            "bh_precompute_tables": [_vp, P(TableDesc), _vp, P(_vp)],
+            "bh_tables_upload": [_vp, P(TableDesc), P(C.c_double), P(C.c_double), _vp, P(_vp)],
+            "bh_tables_copy_out": [_vp, P(C.c_double), P(C.c_double)],
+            "bh_tables_copy_colour": [_vp, P(C.c_float), P(C.c_float)],
+            "bh_build_star_cubemap": [_vp, _vp, C.c_longlong, C.c_int, C.c_int, C.c_int, _vp,
+                                      P(_vp)],
+            "bh_cubemap_copy_out": [_vp, P(C.c_uint16), C.c_longlong],
+            "bh_render": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
+            "bh_render_debug": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp, _vp],
+            "bh_render_to_host": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
+            "bh_render_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
+                                P(_vp), _vp],
+            "bh_autotune_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
+                                  P(_vp), P(C.c_int)],
+            "bh_serve_submit": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading), _vp,
+                                P(C.c_ulonglong)],
+            "bh_serve_poll": [_vp, C.c_ulonglong, C.c_int, P(C.c_double)],
+            "bh_serve_flush": [_vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            if args is None:
+                fn.argtypes = [_vp]
+                fn.restype = None
+            else:
+                fn.argtypes = args
+                fn.restype = C.c_int
+        L.bh_last_error.restype = C.c_char_p
+        L.bh_last_error.argtypes = []
+        L.bh_kernel_launches.restype = C.c_longlong
+        L.bh_kernel_launches.argtypes = [_vp]
+        L.bh_cubemap_records.restype = C.c_longlong
+        L.bh_cubemap_records.argtypes = [C.c_int]
+        L.bh_tables_free.argtypes = [_vp]
+        L.bh_tables_free.restype = None
+        L.bh_cubemap_free.argtypes = [_vp]
+        L.bh_cubemap_free.restype = None
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in dir(lib()) if n.startswith("bh_")]
+
+
+def _check(status: int, allow=()):
+    if status != BH_OK and status not in allow:
+        raise BhError(status, lib().bh_last_error().decode())
+    return status
+
+
+def _ptr(x) -> int | None:
+    """Device pointer of a torch tensor, or an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError(f"not a stream: {type(s)}")
+
+
+# ---------------------------------------------------------------------------
+# struct helpers
+# ---------------------------------------------------------------------------
+
+def make_camera(cam: dict) -> Camera:
+    c = Camera()
+    c.r, c.theta, c.phi = cam["r"], cam["theta"], cam["phi"]
+    for k in range(3):
+        c.v[k] = cam["v"][k]
+    o = np.asarray(cam["orient"], dtype=np.float64).reshape(9)
+    for k in range(9):
+        c.orient[k] = o[k]
+    c.fov_y, c.width, c.height = cam["fov_y"], cam["width"], cam["height"]
+    return c
+
+
+def make_disc(d: dict) -> Disc:
+    x = Disc()
+    x.r_in, x.r_out, x.t_peak_K, x.density = d["r_in"], d["r_out"], d["t_peak"], d["density"]
+    x.enabled = int(d.get("enabled", 1))
+    return x
+
+
+def make_shading(exposure_disc=1.0, exposure_stars=0.01) -> Shading:
+    return Shading(exposure_disc, exposure_stars)
+
+
+def _as(obj, maker):
+    return obj if not isinstance(obj, dict) else maker(obj)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI entry points
+# ---------------------------------------------------------------------------
+
+def bh_last_error() -> str:
+    return lib().bh_last_error().decode()
+
+
+def bh_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    out = _vp()
+    _check(lib().bh_create(device, hbm_budget_bytes, C.byref(out)))
+    return out.value
+
+
+def bh_destroy(ctx: int) -> None:
+    lib().bh_destroy(ctx)
+
+
+def bh_kernel_launches(ctx: int) -> int:
+    return lib().bh_kernel_launches(ctx)
+
+
+def bh_precompute_tables(ctx: int, d_n=512, u_ne=64, u_nphi=32, storage=BH_F32,
+                         stream=None) -> int:
+    desc = TableDesc(d_n, u_ne, u_nphi, storage)
+    out = _vp()
+    _check(lib().bh_precompute_tables(ctx, C.byref(desc), _stream(stream), C.byref(out)))
+    return out.value
+
+
+def bh_tables_upload(ctx: int, D: np.ndarray, U: np.ndarray, storage=BH_F32, stream=None) -> int:
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    desc = TableDesc(D.shape[0], U.shape[1], U.shape[0], storage)
+    out = _vp()
+    _check(lib().bh_tables_upload(ctx, C.byref(desc), D.ctypes.data_as(C.POINTER(C.c_double)),
+                                  U.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream),
+                                  C.byref(out)))
+    return out.value
+
+
+def bh_tables_copy_out(tables: int, d_n: int, u_ne: int, u_nphi: int):
+    D = np.zeros((d_n, d_n))
+    U = np.zeros((u_nphi, u_ne))
+    _check(lib().bh_tables_copy_out(tables, D.ctypes.data_as(C.POINTER(C.c_double)),
+                                    U.ctypes.data_as(C.POINTER(C.c_double))))
+    return D, U
+
+
+def bh_tables_copy_colour(tables: int):
+    Ct = np.zeros((64, 32, 64, 4), dtype=np.float32)
+    dt = np.zeros((1024, 4), dtype=np.float32)
+    _check(lib().bh_tables_copy_colour(tables, Ct.ctypes.data_as(C.POINTER(C.c_float)),
+                                       dt.ctypes.data_as(C.POINTER(C.c_float))))
+    return Ct, dt
+
+
+def bh_tables_free(tables: int) -> None:
+    lib().bh_tables_free(tables)
+
+
+def bh_build_star_cubemap(ctx: int, stars, face_size: int, storage=BH_F16, stream=None) -> int:
+    """stars: (n, 5) float32 numpy array (host) or a torch CUDA tensor (device)."""
+    out = _vp()
+    if hasattr(stars, "is_cuda") and stars.is_cuda:
+        assert stars.dtype.itemsize == 4 and stars.shape[-1] == 5 and stars.is_contiguous()
+        n, ptr, on_dev = stars.shape[0], stars.data_ptr(), 1
+        keep = stars
+    else:
+        keep = np.ascontiguousarray(stars, dtype=np.float32)
+        assert keep.ndim == 2 and keep.shape[1] == 5
+        n, ptr, on_dev = keep.shape[0], keep.ctypes.data, 0
+    _check(lib().bh_build_star_cubemap(ctx, ptr, n, face_size, storage, on_dev, _stream(stream),
+                                       C.byref(out)))
+    del keep
+    return out.value
+
+
+def bh_cubemap_records(face_size: int) -> int:
+    return lib().bh_cubemap_records(face_size)
+
+
+def bh_cubemap_copy_out(cube: int, face_size: int) -> np.ndarray:
+    n = bh_cubemap_records(face_size)
+    rec = np.zeros((n, 4), dtype=np.uint16)
+    _check(lib().bh_cubemap_copy_out(cube, rec.ctypes.data_as(C.POINTER(C.c_uint16)), n))
+    return rec
+
+
+def bh_cubemap_free(cube: int) -> None:
+    lib().bh_cubemap_free(cube)
+
+
+def bh_render(ctx, tables, cube, camera, disc, shading, out, stream=None) -> None:
+    cam = _as(camera, make_camera)
+    d = _as(disc, make_disc)
+    _check(lib().bh_render(ctx, tables, cube, C.byref(cam), C.byref(d), C.byref(shading),
+                           _ptr(out), _stream(stream)))
+
+
+def bh_render_debug(ctx, tables, cube, camera, disc, shading, out, dbg, stream=None) -> None:
+    cam = _as(camera, make_camera)
+    d = _as(disc, make_disc)
+    _check(lib().bh_render_debug(ctx, tables, cube, C.byref(cam), C.byref(d), C.byref(shading),
+                                 _ptr(out), _ptr(dbg), _stream(stream)))
+
+
+def bh_render_to_host(ctx, tables, cube, camera, disc, shading, out_host: np.ndarray,
+                      stream=None) -> None:
+    cam = _as(camera, make_camera)
+    d = _as(disc, make_disc)
+    if isinstance(out_host, np.ndarray):
+        assert out_host.dtype == np.float32 and out_host.flags["C_CONTIGUOUS"]
+        assert out_host.size >= cam.width * cam.height * 4
+        p = out_host.ctypes.data
+    else:  # pinned torch CPU tensor
+        assert out_host.numel() >= cam.width * cam.height * 4
+        p = out_host.data_ptr()
+    _check(lib().bh_render_to_host(ctx, tables, cube, C.byref(cam), C.byref(d),
+                                   C.byref(shading), p, _stream(stream)))
+
+
+def _cams(cameras):
+    arr = (Camera * len(cameras))()
+    for k, c in enumerate(cameras):
+        arr[k] = _as(c, make_camera)
+    return arr
+
+
+def bh_render_batch(ctx, tables, cube, cameras, disc, shading, outs, stream=None) -> None:
+    n = len(cameras)
+    cams = _cams(cameras)
+    ptrs = (_vp * n)(*[_ptr(o) for o in outs])
+    d = _as(disc, make_disc)
+    _check(lib().bh_render_batch(ctx, tables, cube, n, cams, C.byref(d), C.byref(shading), ptrs,
+                                 _stream(stream)))
+
+
+def bh_autotune_batch(ctx, tables, cube, cameras, disc, shading, outs) -> int:
+    n = len(cameras)
+    cams = _cams(cameras)
+    ptrs = (_vp * n)(*[_ptr(o) for o in outs])
+    d = _as(disc, make_disc)
+    chosen = C.c_int(-1)
+    _check(lib().bh_autotune_batch(ctx, tables, cube, n, cams, C.byref(d), C.byref(shading),
+                                   ptrs, C.byref(chosen)))
+    return chosen.value
+
+
+def bh_serve_submit(ctx, tables, cube, viewer, camera, disc, shading, out):
+    """Returns (status, ticket); status is BH_OK or BH_ERR_BUSY (admission refused)."""
+    cam = _as(camera, make_camera)
+    d = _as(disc, make_disc)
+    t = C.c_ulonglong(0)
+    st = _check(lib().bh_serve_submit(ctx, tables, cube, viewer, C.byref(cam), C.byref(d),
+                                      C.byref(shading), _ptr(out), C.byref(t)),
+                allow=(BH_ERR_BUSY,))
+    return st, t.value
+
+
+def bh_serve_poll(ctx, ticket, timeout_us=0):
+    """Returns (status, latency_ms); status is BH_OK or BH_ERR_NOT_READY."""
+    lat = C.c_double(0.0)
+    st = _check(lib().bh_serve_poll(ctx, ticket, timeout_us, C.byref(lat)),
+                allow=(BH_ERR_NOT_READY,))
+    return st, lat.value
+
+
+def bh_serve_flush(ctx) -> None:
+    _check(lib().bh_serve_flush(ctx))

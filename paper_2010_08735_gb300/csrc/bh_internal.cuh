@@ -1,0 +1,103 @@
+// Internal declarations shared by the libbh translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/bh.h"
+
+namespace bh {
+
+constexpr double kMu = 4.0 / 27.0;  // max of u^2 (1-u), photon sphere u = 2/3 (Sec. 3.3.1)
+constexpr double kPi = 3.14159265358979323846;
+
+// Sizes of the colour tables (Sec. 3.4.2 and the disc black-body table).
+constexpr int kCnx = 64, kCny = 32, kCnd = 64;
+constexpr int kDiscN = 1024;
+constexpr int kNLambda = 95;  // 360..830 nm, 5 nm trapezoid
+constexpr int kNLocus = 4096;
+constexpr int kMaxUTexels = 4096;
+
+// Status word bits written by kernels (never a trap or an assert).
+constexpr unsigned kStatusMbarTimeout = 1u;
+constexpr unsigned kStatusBadIndex = 2u;
+
+void set_error(const char *fmt, ...);
+bh_status cuda_fail(cudaError_t e, const char *what);
+#define BH_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+struct ServeState;
+
+struct RenderTuning {
+  int warps_per_block = 8;   // block = warps * 32 threads
+  int block_w = 32;          // block tile width in pixels (multiple of 8)
+  int blocks_per_sm = 4;     // persistent grid = SMs * blocks_per_sm
+};
+
+}  // namespace bh
+
+struct bh_ctx {
+  int device = 0;
+  int sm_count = 0;
+  size_t budget = 0;
+  cudaStream_t aux = nullptr;
+  unsigned *status_dev = nullptr;     // kernel status word
+  std::atomic<long long> launches{0};
+  // render staging: per-camera constants for batched launches
+  void *cam_host = nullptr;           // pinned
+  void *cam_dev = nullptr;
+  int cam_cap = 0;
+  void *tile_host = nullptr;          // pinned
+  void *tile_dev = nullptr;
+  int tile_cap = 0;
+  float *frame_dev = nullptr;         // bh_render_to_host frame buffer
+  size_t frame_cap = 0;
+  bh::RenderTuning tuning;
+  bh::ServeState *serve = nullptr;
+  std::mutex mu;
+};
+
+struct bh_tables {
+  bh_ctx *ctx = nullptr;
+  bh_table_desc desc{};
+  double *D64 = nullptr, *U64 = nullptr;  // FP64 values
+  void *D = nullptr, *U = nullptr;        // storage copies read by the renderer
+  float4 *C = nullptr;                    // colour shift table [k][j][i] (XYZ, pad)
+  float4 *disc = nullptr;                 // ln XYZ of black bodies, log2 T in [8, 20]
+};
+
+struct bh_cubemap {
+  bh_ctx *ctx = nullptr;
+  int n = 0;        // face size
+  int levels = 0;
+  bh_dtype storage = BH_F16;
+  uint2 *rec = nullptr;  // all levels
+  long long records = 0;
+};
+
+namespace bh {
+inline long long cube_level_offset(int N, int L) {
+  long long off = 0;
+  for (int l = 0; l < L; ++l) off += 6LL * (N >> l) * (N >> l);
+  return off;
+}
+inline int cube_levels(int N) {
+  int L = 0;
+  while ((1 << L) < N) ++L;
+  return L + 1;
+}
+void count_launch(bh_ctx *ctx, int n = 1);
+bh_status check_status(bh_ctx *ctx, cudaStream_t s);
+bh_status colour_tables_launch(bh_ctx *ctx, bh_tables *t, cudaStream_t s);
+}  // namespace bh

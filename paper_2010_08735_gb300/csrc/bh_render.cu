@@ -1,0 +1,808 @@
+// Per-pixel render (Sec. 3.2-3.4, Algorithm 1 TRACERAY) for sm_103a.
+//
+// Mapping: one thread per pixel; a warp covers an 8x4 pixel tile made of
+// eight 2x2 quads (lane bit 0 = column parity, bit 1 = row parity), so the
+// screen-space derivatives of Sec. 3.3.2 are two warp shuffles (xor 1 and
+// xor 2) with GLSL "fine" semantics.  Blocks are persistent and walk a tile
+// queue that spans every camera of a batch.  The U table (8 KiB) and the
+// disc black-body table (16 KiB) are copied into shared memory once per
+// block by the bulk-copy (TMA) engine behind an mbarrier; the 512x512 D
+// table (1 MiB) and the C(xy,D) table stay in L2 and are read through the
+// read-only path; the star cube map is gathered from L2/HBM with 8-byte
+// records.  Pixels leave as one float4 store each (a warp writes four full
+// 128-byte lines).
+#include <cmath>
+#include <cstring>
+
+#include "bh_internal.cuh"
+
+namespace bh {
+
+constexpr int kMaxLevels = 14;
+
+// Per-camera constants, computed on the host in FP64 (Eq. staticbasis,
+// Eq. camerabasis, the boost B(v) of Appendix C, Eq. d) and rounded to float.
+struct CamConst {
+  float A[9];       // row r (static e_r, e_theta, e_phi), column c (camera e_w, e_h, e_d): spatial parts
+  float b[3];       // spatial part of -e_tau
+  float R[9];       // static orthonormal -> pseudo-Cartesian: columns sqrt(1-u) r^, theta^, phi^
+  float v[3];       // camera velocity on (e_r, e_theta, e_phi)
+  float x[3];       // e_x' = position direction r^
+  float zdeg[3];    // e_z' for radial beams (reading C8)
+  float gamma, f, u, inv_sqrt_1mu;
+  float half_w, half_h;
+  int width, height;
+  int tiles_x, tile0;
+  float4 *out;
+  float *dbg;
+};
+
+struct RenderParams {
+  CamConst cam0;            // single-camera launches
+  const CamConst *cams;     // batched launches (nullptr: cam0)
+  int ncams, total_tiles;
+  int bw, bh, warps_x;      // block tile (pixels) and warps across
+  const void *D;
+  int d_n;
+  const void *U;
+  int u_ne, u_nphi, u_bytes;
+  const float4 *C;
+  const float4 *disc;
+  const uint2 *cube;
+  int cube_n, cube_levels, cube_bf16;
+  long long level_off[kMaxLevels];
+  float u_ic, u_oc, t_peak, rho;
+  float fmax_disc;          // max of u^3 (1 - sqrt(3u)), at u = 12/49
+  int disc_on;
+  float exp_disc, exp_stars;
+  float M[9];               // XYZ -> linear sRGB
+  unsigned *status;
+};
+
+__device__ __forceinline__ float ld_tab(const float *p, int i) { return __ldg(p + i); }
+__device__ __forceinline__ float ld_tab(const __half *p, int i) { return __half2float(__ldg(p + i)); }
+__device__ __forceinline__ float sm_tab(const float *p, int i) { return p[i]; }
+__device__ __forceinline__ float sm_tab(const __half *p, int i) { return __half2float(p[i]); }
+
+constexpr float kMuF = 4.0f / 27.0f;
+constexpr float kPiF = 3.14159265358979f;
+
+// Bilinear D lookup at Appendix A coordinates; x clamped to its branch (C2).
+template <typename DT>
+__device__ __forceinline__ float d_bilinear(const DT *D, int n, float fx, float fy, int xlo, int xhi) {
+  fx = fminf(fmaxf(fx, (float)xlo), (float)xhi);
+  fy = fminf(fmaxf(fy, 0.f), (float)(n - 1));
+  int i0 = (int)fx, j0 = (int)fy;
+  int i1 = min(i0 + 1, xhi), j1 = min(j0 + 1, n - 1);
+  float tx = fx - i0, ty = fy - j0;
+  float a = ld_tab(D, j0 * n + i0), b = ld_tab(D, j0 * n + i1);
+  float c = ld_tab(D, j1 * n + i0), d = ld_tab(D, j1 * n + i1);
+  float lo = fmaf(tx, b - a, a), hi = fmaf(tx, d - c, c);
+  return fmaf(ty, hi - lo, lo);
+}
+
+// x coordinate of D for e^2 (em = e^2 - mu, formed without cancellation).
+__device__ __forceinline__ float d_x(float e2, float em) {
+  if (em < 0.f) {
+    float r = e2 / kMuF;  // 1 - eta
+    float lg = r < 0.5f ? log1pf(-r) : logf(-em / kMuF);
+    return 0.5f - sqrtf(fmaxf(-lg, 0.f) * 0.02f);
+  }
+  float r = kMuF / e2;  // 1 - (e^2 - mu)/e^2
+  float lg = r < 0.5f ? log1pf(-r) : logf(em / e2);
+  return 0.5f + sqrtf(fmaxf(-lg, 0.f) * 0.02f);
+}
+
+template <typename DT, bool DEBUG>
+__global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long mbar;
+  float4 *s_disc = reinterpret_cast<float4 *>(smem);
+  const DT *s_U = reinterpret_cast<const DT *>(smem + sizeof(float4) * kDiscN);
+
+  // ---- stage U and the disc table into shared memory with the bulk-copy engine
+  unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+  if (threadIdx.x == 0) {
+    unsigned bytes = (unsigned)(sizeof(float4) * kDiscN + P.u_bytes);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+    unsigned dst0 = (unsigned)__cvta_generic_to_shared(s_disc);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst0),
+        "l"(P.disc), "r"((unsigned)(sizeof(float4) * kDiscN)), "r"(mb)
+        : "memory");
+    unsigned dst1 = (unsigned)__cvta_generic_to_shared(s_U);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst1),
+        "l"(P.U), "r"((unsigned)P.u_bytes), "r"(mb)
+        : "memory");
+  }
+  __syncthreads();
+  {
+    unsigned done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+          : "=r"(done)
+          : "r"(mb)
+          : "memory");
+    }
+    // every thread of the block sees the same barrier; a timeout means the copy never landed
+    if (!done) {
+      if (threadIdx.x == 0) atomicOr(P.status, kStatusMbarTimeout);
+      return;
+    }
+  }
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = ((lane >> 2) & 3) * 2 + (lane & 1);
+  const int ly = ((lane >> 4) & 1) * 2 + ((lane >> 1) & 1);
+  const int wx = warp % P.warps_x, wy = warp / P.warps_x;
+  const int dn = P.d_n;
+  const DT *D = reinterpret_cast<const DT *>(P.D);
+  const int n_half = dn / 2;
+
+  // peak-temperature luminance for the disc normalisation
+  float y_peak;
+  {
+    float f = (log2f(P.t_peak) - 8.f) / 12.f * kDiscN - 0.5f;
+    f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
+    int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
+    float t = f - k0;
+    y_peak = expf(fmaf(t, s_disc[k1].y - s_disc[k0].y, s_disc[k0].y));
+  }
+
+  for (int tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+    // ---- which camera and which tile of it
+    const CamConst *cp = &P.cam0;
+    if (P.cams) {
+      int lo = 0, hi = P.ncams - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&P.cams[mid].tile0) <= tile) lo = mid; else hi = mid - 1;
+      }
+      cp = P.cams + lo;
+    }
+    const CamConst &C = *cp;
+    int t = tile - C.tile0;
+    int ty = t / C.tiles_x, tx = t - ty * C.tiles_x;
+    int px = tx * P.bw + wx * 8 + lx, py = ty * P.bh + wy * 4 + ly;
+
+    // ---- beam initialisation (Eq. d, Eq. raybasis, Eq. alpha)
+    float qw = (px + 0.5f) - C.half_w, qh = C.half_h - (py + 0.5f);
+    float inv = rsqrtf(fmaf(qw, qw, fmaf(qh, qh, C.f * C.f)));
+    float q0 = qw * inv, q1 = qh * inv, q2 = -C.f * inv;
+    float ds0 = fmaf(C.A[0], q0, fmaf(C.A[1], q1, fmaf(C.A[2], q2, C.b[0])));
+    float ds1 = fmaf(C.A[3], q0, fmaf(C.A[4], q1, fmaf(C.A[5], q2, C.b[1])));
+    float ds2 = fmaf(C.A[6], q0, fmaf(C.A[7], q1, fmaf(C.A[8], q2, C.b[2])));
+    float dsn = sqrtf(fmaf(ds0, ds0, fmaf(ds1, ds1, ds2 * ds2)));
+    float dcam = C.gamma * (1.f + fmaf(C.v[0], ds0, fmaf(C.v[1], ds1, C.v[2] * ds2)) / dsn);
+    float d0 = fmaf(C.R[0], ds0, fmaf(C.R[1], ds1, C.R[2] * ds2));
+    float d1 = fmaf(C.R[3], ds0, fmaf(C.R[4], ds1, C.R[5] * ds2));
+    float d2 = fmaf(C.R[6], ds0, fmaf(C.R[7], ds1, C.R[8] * ds2));
+    const float x0 = C.x[0], x1 = C.x[1], x2 = C.x[2];
+    float c0 = x1 * d2 - x2 * d1, c1 = x2 * d0 - x0 * d2, c2 = x0 * d1 - x1 * d0;
+    float cn = sqrtf(fmaf(c0, c0, fmaf(c1, c1, c2 * c2)));
+    float cosd = fmaf(x0, d0, fmaf(x1, d1, x2 * d2));
+    float dd = sqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+    float delta = atan2f(cn, cosd);
+    float z0, z1, z2;
+    if (cn < 1e-7f * dd) {
+      z0 = C.zdeg[0]; z1 = C.zdeg[1]; z2 = C.zdeg[2];
+    } else {
+      float ic = 1.f / cn;
+      z0 = c0 * ic; z1 = c1 * ic; z2 = c2 * ic;
+    }
+    float y0 = z1 * x2 - z2 * x1, y1 = z2 * x0 - z0 * x2, y2 = z0 * x1 - z1 * x0;
+    bool alpha_ok = false;
+    float alpha = 0.f;
+    {
+      float t0 = -z1, t1 = z0;
+      float tn = sqrtf(fmaf(t0, t0, t1 * t1));
+      if (tn > 1e-12f) {
+        // t = +-(e_z ^ e_z')/|.| with t . e_y' >= 0; alpha = angle from e_x' to t
+        float ty_ = (t0 * y0 + t1 * y1) / tn, tx_ = (t0 * x0 + t1 * x1) / tn;
+        if (ty_ < 0.f) { ty_ = -ty_; tx_ = -tx_; }
+        alpha = atan2f(ty_, tx_);
+        alpha_ok = true;
+      }
+    }
+
+    // ---- TRACERAY (Algorithm 1)
+    const float u = C.u;
+    float udot = -u * cosd / fmaxf(cn, 1e-30f);
+    float um = u - 2.f / 3.f;
+    float em = fmaf(udot, udot, -um * um * (u + 1.f / 3.f));  // e^2 - mu
+    float e2 = kMuF + em;
+    bool captured = false;
+    int nh = 0;
+    float hu0 = 0.f, hu1 = 0.f;
+    float delta_p = 0.f;
+    if (em < 0.f && u > 2.f / 3.f) {
+      captured = true;
+    } else {
+      int s = udot > 0.f ? 1 : -1;
+      float xd = d_x(e2, em);
+      float fx = xd * (dn - 1);
+      int xlo = em < 0.f ? 0 : n_half, xhi = em < 0.f ? n_half - 1 : dn - 1;
+      float ua = 0.f, Dl, Da = 0.f, phia = INFINITY;
+      if (em < 0.f) {
+        float eta = -em / kMuF;
+        float sa = asinf(sqrtf(fminf(eta, 1.f)));
+        float th = (0.5f * kPiF - 2.f * sa) * (1.f / 3.f);
+        ua = 1.f / 3.f + 2.f / 3.f * sinf(th);
+        float yv = 1.f - sqrtf(fmaxf(1.f - u / ua, 0.f));
+        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
+        Da = d_bilinear(D, dn, fx, (float)(dn - 1), xlo, xhi);
+        phia = Da + 0.5f * kPiF;
+      } else {
+        const float r23 = 0.81649658f, r13 = 0.57735027f;
+        float sq = sqrtf(fabsf(um));
+        float yv = (r23 + (um >= 0.f ? sq : -sq)) / (r23 + r13);
+        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
+      }
+      if (alpha_ok && P.disc_on) {
+        float e = sqrtf(e2);
+        float ux = 1.f / fmaf(6.f, e2, 1.f);
+        float yk = (1.f + 6.f * e2 * e) / (3.f * (1.f + e2));
+        float fxu = fminf(fmaxf(ux * (P.u_ne - 1), 0.f), (float)(P.u_ne - 1));
+        int ui0 = (int)fxu, ui1 = min(ui0 + 1, P.u_ne - 1);
+        float utx = fxu - ui0;
+        auto ulook = [&](float ph) {
+          float fy = fminf(fmaxf(ph * yk * (P.u_nphi - 1), 0.f), (float)(P.u_nphi - 1));
+          int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
+          float ty2 = fy - j0;
+          float a = sm_tab(s_U, j0 * P.u_ne + ui0), b = sm_tab(s_U, j0 * P.u_ne + ui1);
+          float c = sm_tab(s_U, j1 * P.u_ne + ui0), d = sm_tab(s_U, j1 * P.u_ne + ui1);
+          float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
+          return fmaf(ty2, hi - lo, lo);
+        };
+        float phi = Dl + (s == 1 ? kPiF - delta : delta) + s * alpha;
+        float phi0 = phi - kPiF * floorf(phi / kPiF);
+        float u0 = ulook(phi0);
+        if (phi0 < phia && P.u_oc <= u0 && u0 <= P.u_ic && ((s == 1 && u0 > u) || (s == -1 && u0 < u))) {
+          hu0 = u0;
+          nh = 1;
+        }
+        if (em < 0.f && s == 1) {
+          phi = 2.f * phia - phi;
+          float phi1 = phi - kPiF * floorf(phi / kPiF);
+          float u1 = ulook(phi1);
+          if (phi1 < phia && P.u_oc <= u1 && u1 <= P.u_ic) {
+            if (nh == 0) hu0 = u1; else hu1 = u1;
+            ++nh;
+          }
+        }
+      }
+      if (udot > 0.f) {
+        if (em < 0.f) delta_p = delta + 2.f * Da - Dl;
+        else captured = true;
+      } else {
+        delta_p = delta + Dl;
+      }
+    }
+
+    // ---- disc hits, front to back (Sec. 3.3.3, 3.4.2)
+    float LX = 0.f, LY = 0.f, LZ = 0.f, trans = 1.f;
+    float dop0 = 0.f, dop1 = 0.f;
+    if (nh > 0) {
+      float e = sqrtf(e2);
+      float sc = P.rho * P.exp_disc / y_peak;
+      for (int h = 0; h < nh; ++h) {
+        float up = h == 0 ? hu0 : hu1;
+        float fu = up * up * up * (1.f - sqrtf(3.f * up));
+        float T = fu > 0.f ? P.t_peak * sqrtf(sqrtf(fu / P.fmax_disc)) : 0.f;
+        float bp = sqrtf(up / (2.f * (1.f - up)));
+        float gp = rsqrtf(1.f - bp * bp);
+        float bd = bp * (up * sqrtf(1.f - up) / e) * z2;
+        float Dk = dcam / (gp * (1.f + bd)) * sqrtf(1.f - up) * C.inv_sqrt_1mu;
+        if (h == 0) dop0 = Dk; else dop1 = Dk;
+        float TT = Dk * T;
+        if (TT >= 256.f) {
+          float f = (log2f(TT) - 8.f) / 12.f * kDiscN - 0.5f;
+          f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
+          int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
+          float tt = f - k0;
+          float4 a = s_disc[k0], b = s_disc[k1];
+          float w = trans * sc;
+          LX = fmaf(w, expf(fmaf(tt, b.x - a.x, a.x)), LX);
+          LY = fmaf(w, expf(fmaf(tt, b.y - a.y, a.y)), LY);
+          LZ = fmaf(w, expf(fmaf(tt, b.z - a.z, a.z)), LZ);
+        }
+        trans *= 1.f - P.rho;
+      }
+    }
+
+    // ---- escape direction and its screen-space derivatives (quad shuffles)
+    float sd, cdp;
+    sincosf(delta_p, &sd, &cdp);
+    float dp0 = captured ? 0.f : fmaf(cdp, x0, sd * y0);
+    float dp1 = captured ? 0.f : fmaf(cdp, x1, sd * y1);
+    float dp2 = captured ? 0.f : fmaf(cdp, x2, sd * y2);
+    unsigned capbits = __ballot_sync(0xffffffffu, captured);
+    bool anycap = ((capbits >> (lane & ~3)) & 0xfu) != 0u;
+    const bool colodd = lane & 1, rowodd = (lane >> 1) & 1;
+    auto dw = [&](float v) { float o = __shfl_xor_sync(0xffffffffu, v, 1); return colodd ? v - o : o - v; };
+    auto dh = [&](float v) { float o = __shfl_xor_sync(0xffffffffu, v, 2); return rowodd ? o - v : v - o; };
+    float dw0 = dw(dp0), dw1 = dw(dp1), dw2 = dw(dp2);
+    float dh0 = dh(dp0), dh1 = dh(dp1), dh2 = dh(dp2);
+    float qw0 = dw(q0), qw1 = dw(q1), qw2 = dw(q2);
+    float qh0 = dh(q0), qh1 = dh(q1), qh2 = dh(q2);
+
+    // ---- star gather over the beam footprint (Sec. 3.3.2) and lensing (Sec. 3.4.1)
+    float omega = 0.f, dstar = 0.f, SX = 0.f, SY = 0.f, SZ = 0.f;
+    int level = -1, face = -1, visited = 0;
+    if (!anycap && P.cube) {
+      float cq0 = qw1 * qh2 - qw2 * qh1, cq1 = qw2 * qh0 - qw0 * qh2, cq2 = qw0 * qh1 - qw1 * qh0;
+      float cd0 = dw1 * dh2 - dw2 * dh1, cd1 = dw2 * dh0 - dw0 * dh2, cd2 = dw0 * dh1 - dw1 * dh0;
+      float den = sqrtf(fmaf(cd0, cd0, fmaf(cd1, cd1, cd2 * cd2)));
+      if (den > 0.f) {
+        omega = sqrtf(fmaf(cq0, cq0, fmaf(cq1, cq1, cq2 * cq2))) / den;
+        float ax = fabsf(dp0), ay = fabsf(dp1), az = fabsf(dp2);
+        float sc, tc, ma, dmaw, dmah, dscw, dsch, dtcw, dtch;
+        if (ax >= ay && ax >= az) {
+          ma = ax;
+          if (dp0 >= 0.f) { face = 0; sc = -dp2; tc = -dp1; dmaw = dw0; dmah = dh0; dscw = -dw2; dsch = -dh2; dtcw = -dw1; dtch = -dh1; }
+          else { face = 1; sc = dp2; tc = -dp1; dmaw = -dw0; dmah = -dh0; dscw = dw2; dsch = dh2; dtcw = -dw1; dtch = -dh1; }
+        } else if (ay >= az) {
+          ma = ay;
+          if (dp1 >= 0.f) { face = 2; sc = dp0; tc = dp2; dmaw = dw1; dmah = dh1; dscw = dw0; dsch = dh0; dtcw = dw2; dtch = dh2; }
+          else { face = 3; sc = dp0; tc = -dp2; dmaw = -dw1; dmah = -dh1; dscw = dw0; dsch = dh0; dtcw = -dw2; dtch = -dh2; }
+        } else {
+          ma = az;
+          if (dp2 >= 0.f) { face = 4; sc = dp0; tc = -dp1; dmaw = dw2; dmah = dh2; dscw = dw0; dsch = dh0; dtcw = -dw1; dtch = -dh1; }
+          else { face = 5; sc = -dp0; tc = -dp1; dmaw = -dw2; dmah = -dh2; dscw = -dw0; dsch = -dh0; dtcw = -dw1; dtch = -dh1; }
+        }
+        const int N = P.cube_n;
+        float hN = 0.5f * N, ima = 1.f / ma;
+        float sr = sc * ima, tr = tc * ima;
+        float S = (sr + 1.f) * hN, T = (tr + 1.f) * hN;
+        float Jsw = hN * (dscw - sr * dmaw) * ima, Jsh = hN * (dsch - sr * dmah) * ima;
+        float Jtw = hN * (dtcw - tr * dmaw) * ima, Jth = hN * (dtch - tr * dmah) * ima;
+        float hs = fabsf(Jsw) + fabsf(Jsh), ht = fabsf(Jtw) + fabsf(Jth);
+        float hm = fmaxf(hs, ht);
+        int L = 0;
+        while (L < P.cube_levels - 1 && 2.f * hm > 8.f * (float)(1 << L)) ++L;  // <= 9x9 texels (C17)
+        level = L;
+        float sL = 1.f / (float)(1 << L);
+        int NL = N >> L;
+        float cS = S * sL, cT = T * sL, hsL = hs * sL, htL = ht * sL;
+        float a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
+        float det = a11 * a22 - a12 * a21;
+        if (fabsf(det) > 1e-6f * sqrtf((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22))) {
+          float id = 1.f / det;
+          float i11 = a22 * id, i12 = -a12 * id, i21 = -a21 * id, i22 = a11 * id;
+          int i0 = max((int)floorf(cS - hsL), 0), i1 = min((int)floorf(cS + hsL), NL - 1);
+          int j0 = max((int)floorf(cT - htL), 0), j1 = min((int)floorf(cT + htL), NL - 1);
+          const uint2 *rec = P.cube + P.level_off[L] + (long long)face * NL * NL;
+          float lscale = (float)(1 << (2 * L));
+          for (int jj = j0; jj <= j1; ++jj) {
+            float dt = (jj - cT);
+            for (int ii = i0; ii <= i1; ++ii) {
+              ++visited;
+              uint2 r = __ldg(rec + (long long)jj * NL + ii);
+              float X, Y, Z;
+              if (P.cube_bf16) {
+                X = __uint_as_float(r.x << 16);
+                Y = __uint_as_float(r.x & 0xffff0000u);
+                Z = __uint_as_float(r.y << 16);
+              } else {
+                X = __half2float(__ushort_as_half((unsigned short)(r.x & 0xffffu)));
+                Y = __half2float(__ushort_as_half((unsigned short)(r.x >> 16)));
+                Z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
+              }
+              if (X + Y + Z <= 0.f) continue;
+              unsigned pw = r.y >> 16;
+              float ds_ = (ii - cS) + ((pw & 255u) + 0.5f) * (1.f / 256.f);
+              float dt_ = dt + ((pw >> 8) + 0.5f) * (1.f / 256.f);
+              float w = fmaf(i11, ds_, i12 * dt_), h = fmaf(i21, ds_, i22 * dt_);
+              float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
+              if (fw <= 0.f || fh <= 0.f) continue;
+              float wt = fw * fh * lscale;
+              SX = fmaf(wt, X, SX);
+              SY = fmaf(wt, Y, SY);
+              SZ = fmaf(wt, Z, SZ);
+            }
+          }
+        }
+      }
+      dstar = dcam * C.inv_sqrt_1mu;  // static star at infinity: u' = 0
+      float Ssum = SX + SY + SZ;
+      if (Ssum > 0.f) {
+        // C(xy, D): trilinear, texel centres, clamped
+        float fx = ((SX / Ssum) - 0.15f) * (kCnx / 0.60f) - 0.5f;
+        float fy = ((SY / Ssum) - 0.15f) * (kCny / 0.35f) - 0.5f;
+        float fz = (log2f(dstar) + 4.f) * (kCnd / 8.f) - 0.5f;
+        fx = fminf(fmaxf(fx, 0.f), kCnx - 1.f);
+        fy = fminf(fmaxf(fy, 0.f), kCny - 1.f);
+        fz = fminf(fmaxf(fz, 0.f), kCnd - 1.f);
+        int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
+        int i1 = min(i0 + 1, kCnx - 1), j1 = min(j0 + 1, kCny - 1), k1 = min(k0 + 1, kCnd - 1);
+        float tx2 = fx - i0, ty2 = fy - j0, tz2 = fz - k0;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
+#pragma unroll
+        for (int cidx = 0; cidx < 8; ++cidx) {
+          int ii = (cidx & 1) ? i1 : i0, jj = (cidx & 2) ? j1 : j0, kk = (cidx & 4) ? k1 : k0;
+          float w = ((cidx & 1) ? tx2 : 1.f - tx2) * ((cidx & 2) ? ty2 : 1.f - ty2) * ((cidx & 4) ? tz2 : 1.f - tz2);
+          float4 cv = __ldg(P.C + ((kk * kCny + jj) * kCnx + ii));
+          cx = fmaf(w, cv.x, cx);
+          cy = fmaf(w, cv.y, cy);
+          cz = fmaf(w, cv.z, cz);
+        }
+        float sc = Ssum * omega * P.exp_stars * trans;
+        LX = fmaf(sc, cx, LX);
+        LY = fmaf(sc, cy, LY);
+        LZ = fmaf(sc, cz, LZ);
+      }
+    }
+
+    // ---- store
+    if (px < C.width && py < C.height) {
+      float R_ = fmaf(P.M[0], LX, fmaf(P.M[1], LY, P.M[2] * LZ));
+      float G_ = fmaf(P.M[3], LX, fmaf(P.M[4], LY, P.M[5] * LZ));
+      float B_ = fmaf(P.M[6], LX, fmaf(P.M[7], LY, P.M[8] * LZ));
+      long long o = (long long)py * C.width + px;
+      C.out[o] = make_float4(R_, G_, B_, 1.f);
+      if (DEBUG) {
+        float *g = C.dbg + o * 16;
+        float4 *g4 = reinterpret_cast<float4 *>(g);
+        g4[0] = make_float4(e2, delta, captured ? INFINITY : delta_p, (float)nh);
+        g4[1] = make_float4(hu0, hu1, (float)(anycap ? -1 : level), (float)(anycap ? -1 : face));
+        g4[2] = make_float4(omega, dstar, SX, SY);
+        g4[3] = make_float4(SZ, dop0, dop1, (float)visited);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+static bool validate_camera(const bh_camera *c, int idx) {
+  if (!c) { set_error("camera %d is NULL", idx); return false; }
+  if (!(c->r > 1.0) || !std::isfinite(c->r)) {
+    set_error("camera %d: r = %g, must be > 1 (outside the horizon)", idx, c->r);
+    return false;
+  }
+  double v2 = c->v[0] * c->v[0] + c->v[1] * c->v[1] + c->v[2] * c->v[2];
+  if (!(v2 < 1.0)) { set_error("camera %d: |v| = %g, must be < 1", idx, sqrt(v2)); return false; }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += c->orient[i * 3 + k] * c->orient[j * 3 + k];
+      if (fabs(s - (i == j ? 1.0 : 0.0)) > 1e-6) {
+        set_error("camera %d: orientation is not orthonormal", idx);
+        return false;
+      }
+    }
+  if (!(c->fov_y > 0.0 && c->fov_y < kPi)) { set_error("camera %d: fov_y out of (0, pi)", idx); return false; }
+  if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) {
+    set_error("camera %d: size %dx%d out of 1..16384", idx, c->width, c->height);
+    return false;
+  }
+  return true;
+}
+
+static bool validate_disc(const bh_disc *d) {
+  if (!d) { set_error("disc is NULL"); return false; }
+  if (!d->enabled) return true;
+  if (!(d->r_in >= 3.0) || !(d->r_out > d->r_in) || !std::isfinite(d->r_out)) {
+    set_error("disc: need 3 <= r_in < r_out (got %g, %g)", d->r_in, d->r_out);
+    return false;
+  }
+  if (!(d->density >= 0.0 && d->density <= 1.0) || !(d->t_peak_K > 0.0)) {
+    set_error("disc: density in [0,1] and t_peak_K > 0 required");
+    return false;
+  }
+  return true;
+}
+
+// Camera frame in FP64: static basis (Eq. staticbasis), boost B(v) (the
+// camera's 4-velocity is gamma (1, v) on the static frame), user rotation O.
+static void camera_constants(const bh_camera *c, CamConst *k) {
+  double st = sin(c->theta), ct = cos(c->theta), sp = sin(c->phi), cph = cos(c->phi);
+  double u = 1.0 / c->r;
+  double rh[3] = {st * cph, st * sp, ct}, th[3] = {ct * cph, ct * sp, -st}, ph[3] = {-sp, cph, 0.0};
+  const double *v = c->v;
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  double g = 1.0 / sqrt(1.0 - v2);
+  // boosted spatial axes e'_j, static components (t; r, theta, phi)
+  double Bt[3], Bs[3][3];
+  for (int j = 0; j < 3; ++j) {
+    Bt[j] = g * v[j];
+    for (int m = 0; m < 3; ++m) Bs[j][m] = (j == m ? 1.0 : 0.0) + (v2 > 0.0 ? (g - 1.0) * v[j] * v[m] / v2 : 0.0);
+  }
+  (void)Bt;
+  // camera axes e_w, e_h, e_d = O e'
+  double Es[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int m = 0; m < 3; ++m) {
+      double s = 0.0;
+      for (int j = 0; j < 3; ++j) s += c->orient[i * 3 + j] * Bs[j][m];
+      Es[i][m] = s;
+    }
+  for (int r = 0; r < 3; ++r)
+    for (int col = 0; col < 3; ++col) k->A[r * 3 + col] = (float)Es[col][r];
+  for (int r = 0; r < 3; ++r) k->b[r] = (float)(-g * v[r]);
+  double s1 = sqrt(1.0 - u);
+  for (int r = 0; r < 3; ++r) {
+    k->R[r * 3 + 0] = (float)(s1 * rh[r]);
+    k->R[r * 3 + 1] = (float)th[r];
+    k->R[r * 3 + 2] = (float)ph[r];
+    k->v[r] = (float)v[r];
+    k->x[r] = (float)rh[r];
+  }
+  // radial beams (reading C8): e_z' = x ^ (least-aligned axis) / |.|
+  int m = fabs(rh[0]) <= fabs(rh[1]) ? (fabs(rh[0]) <= fabs(rh[2]) ? 0 : 2) : (fabs(rh[1]) <= fabs(rh[2]) ? 1 : 2);
+  double axv[3] = {0, 0, 0};
+  axv[m] = 1.0;
+  double z[3] = {rh[1] * axv[2] - rh[2] * axv[1], rh[2] * axv[0] - rh[0] * axv[2], rh[0] * axv[1] - rh[1] * axv[0]};
+  double zn = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+  for (int r = 0; r < 3; ++r) k->zdeg[r] = (float)(z[r] / zn);
+  k->gamma = (float)g;
+  k->f = (float)(0.5 * c->height / tan(0.5 * c->fov_y));
+  k->u = (float)u;
+  k->inv_sqrt_1mu = (float)(1.0 / s1);
+  k->half_w = (float)(0.5 * c->width);
+  k->half_h = (float)(0.5 * c->height);
+  k->width = c->width;
+  k->height = c->height;
+}
+
+// XYZ -> linear sRGB from the Rec.709 primaries and the D65 white point.
+static void xyz_to_srgb(float *M) {
+  const double px[3] = {0.64, 0.30, 0.15}, py[3] = {0.33, 0.60, 0.06};
+  const double W[3] = {0.3127 / 0.3290, 1.0, (1.0 - 0.3127 - 0.3290) / 0.3290};
+  double P[3][3];
+  for (int c = 0; c < 3; ++c) {
+    P[0][c] = px[c] / py[c];
+    P[1][c] = 1.0;
+    P[2][c] = (1.0 - px[c] - py[c]) / py[c];
+  }
+  // inverse by Gauss-Jordan
+  double a[3][6];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 6; ++c) a[r][c] = c < 3 ? P[r][c] : (c - 3 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 3; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 3; ++r)
+      if (fabs(a[r][c]) > fabs(a[p][c])) p = r;
+    for (int k = 0; k < 6; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+    double d = a[c][c];
+    for (int k = 0; k < 6; ++k) a[c][k] /= d;
+    for (int r = 0; r < 3; ++r)
+      if (r != c) {
+        double f = a[r][c];
+        for (int k = 0; k < 6; ++k) a[r][k] -= f * a[c][k];
+      }
+  }
+  double S[3];
+  for (int r = 0; r < 3; ++r) S[r] = a[r][3] * W[0] + a[r][4] * W[1] + a[r][5] * W[2];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) M[r * 3 + c] = (float)(a[r][3 + c] / S[r]);
+}
+
+static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                             const bh_disc *disc, const bh_shading *sh, RenderParams &P) {
+  memset(&P, 0, sizeof P);
+  P.D = t->D;
+  P.d_n = t->desc.d_n;
+  P.U = t->U;
+  P.u_ne = t->desc.u_ne;
+  P.u_nphi = t->desc.u_nphi;
+  size_t es = t->desc.storage == BH_F32 ? 4 : 2;
+  P.u_bytes = (int)(((size_t)P.u_ne * P.u_nphi * es + 15) / 16 * 16);
+  P.C = t->C;
+  P.disc = t->disc;
+  if (cube) {
+    P.cube = cube->rec;
+    P.cube_n = cube->n;
+    P.cube_levels = cube->levels;
+    P.cube_bf16 = cube->storage == BH_BF16;
+    for (int L = 0; L < cube->levels && L < kMaxLevels; ++L) P.level_off[L] = cube_level_offset(cube->n, L);
+  }
+  P.disc_on = disc->enabled ? 1 : 0;
+  P.u_ic = disc->enabled ? (float)(1.0 / disc->r_in) : 0.f;
+  P.u_oc = disc->enabled ? (float)(1.0 / disc->r_out) : 1.f;
+  P.t_peak = (float)(disc->t_peak_K > 0 ? disc->t_peak_K : 1e4);
+  P.rho = (float)disc->density;
+  P.fmax_disc = (float)(pow(12.0 / 49.0, 3) * (1.0 - sqrt(36.0 / 49.0)));
+  P.exp_disc = sh ? sh->exposure_disc : 1.f;
+  P.exp_stars = sh ? sh->exposure_stars : 0.01f;
+  xyz_to_srgb(P.M);
+  P.status = ctx->status_dev;
+  P.bw = ctx->tuning.block_w;
+  P.warps_x = P.bw / 8;
+  P.bh = 4 * (ctx->tuning.warps_per_block / P.warps_x);
+  return BH_OK;
+}
+
+static bh_status launch(bh_ctx *ctx, const bh_tables *t, RenderParams &P, bool debug, cudaStream_t s) {
+  int threads = 32 * ctx->tuning.warps_per_block;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
+  int grid = std::min(P.total_tiles, ctx->sm_count * ctx->tuning.blocks_per_sm);
+  if (grid < 1) return BH_OK;
+  bool half = t->desc.storage == BH_F16;
+  if (!half && !debug) render_kernel<float, false><<<grid, threads, smem, s>>>(P);
+  else if (!half && debug) render_kernel<float, true><<<grid, threads, smem, s>>>(P);
+  else if (half && !debug) render_kernel<__half, false><<<grid, threads, smem, s>>>(P);
+  else render_kernel<__half, true><<<grid, threads, smem, s>>>(P);
+  count_launch(ctx);
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
+}
+
+static bh_status render_one(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                            const bh_camera *cam, const bh_disc *disc, const bh_shading *sh,
+                            float *out, float *dbg, cudaStream_t s) {
+  if (!ctx || !t || !out) { set_error("bh_render: NULL argument"); return BH_ERR_INVALID_ARG; }
+  if (((uintptr_t)out & 15) || (dbg && ((uintptr_t)dbg & 15))) {
+    set_error("bh_render: output buffers must be 16-byte aligned");
+    return BH_ERR_INVALID_ARG;
+  }
+  if (!validate_camera(cam, 0) || !validate_disc(disc)) return BH_ERR_INVALID_ARG;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  RenderParams P;
+  fill_params(ctx, t, cube, disc, sh, P);
+  camera_constants(cam, &P.cam0);
+  P.cam0.tiles_x = (cam->width + P.bw - 1) / P.bw;
+  P.cam0.tile0 = 0;
+  P.cam0.out = reinterpret_cast<float4 *>(out);
+  P.cam0.dbg = dbg;
+  P.cams = nullptr;
+  P.ncams = 1;
+  P.total_tiles = P.cam0.tiles_x * ((cam->height + P.bh - 1) / P.bh);
+  return launch(ctx, t, P, dbg != nullptr, s);
+}
+
+static bh_status ensure_cam_staging(bh_ctx *ctx, int n) {
+  if (n <= ctx->cam_cap) return BH_OK;
+  if (ctx->cam_host) cudaFreeHost(ctx->cam_host);
+  if (ctx->cam_dev) cudaFree(ctx->cam_dev);
+  ctx->cam_host = ctx->cam_dev = nullptr;
+  ctx->cam_cap = 0;
+  int cap = std::max(n, 64);
+  BH_CUDA(cudaMallocHost(&ctx->cam_host, sizeof(CamConst) * cap));
+  BH_CUDA(cudaMalloc(&ctx->cam_dev, sizeof(CamConst) * cap));
+  ctx->cam_cap = cap;
+  return BH_OK;
+}
+
+bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
+                            const bh_camera *cams, const bh_disc *disc, const bh_shading *sh,
+                            float *const *outs, cudaStream_t s, void *cam_host, void *cam_dev) {
+  RenderParams P;
+  fill_params(ctx, t, cube, disc, sh, P);
+  CamConst *h = static_cast<CamConst *>(cam_host);
+  int tiles = 0;
+  for (int k = 0; k < n; ++k) {
+    camera_constants(&cams[k], &h[k]);
+    h[k].tiles_x = (cams[k].width + P.bw - 1) / P.bw;
+    h[k].tile0 = tiles;
+    h[k].out = reinterpret_cast<float4 *>(outs[k]);
+    h[k].dbg = nullptr;
+    tiles += h[k].tiles_x * ((cams[k].height + P.bh - 1) / P.bh);
+  }
+  BH_CUDA(cudaMemcpyAsync(cam_dev, h, sizeof(CamConst) * n, cudaMemcpyHostToDevice, s));
+  P.cams = static_cast<const CamConst *>(cam_dev);
+  P.ncams = n;
+  P.total_tiles = tiles;
+  return launch(ctx, t, P, false, s);
+}
+
+size_t cam_const_size() { return sizeof(CamConst); }
+
+bh_status validate_batch(int n, const bh_camera *cams, const bh_disc *disc, float *const *outs) {
+  if (n < 1 || !cams || !outs) { set_error("batch: n >= 1 cameras and outputs required"); return BH_ERR_INVALID_ARG; }
+  for (int k = 0; k < n; ++k) {
+    if (!validate_camera(&cams[k], k)) return BH_ERR_INVALID_ARG;
+    if (!outs[k] || ((uintptr_t)outs[k] & 15)) {
+      set_error("batch: output %d is NULL or not 16-byte aligned", k);
+      return BH_ERR_INVALID_ARG;
+    }
+  }
+  if (!validate_disc(disc)) return BH_ERR_INVALID_ARG;
+  return BH_OK;
+}
+
+}  // namespace bh
+
+using namespace bh;
+
+extern "C" bh_status bh_render(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                               const bh_camera *cam, const bh_disc *disc, const bh_shading *sh,
+                               float *out, void *stream) {
+  return render_one(ctx, t, cube, cam, disc, sh, out, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                                     const bh_camera *cam, const bh_disc *disc,
+                                     const bh_shading *sh, float *out, float *dbg, void *stream) {
+  if (!dbg) { set_error("bh_render_debug: dbg is NULL"); return BH_ERR_INVALID_ARG; }
+  return render_one(ctx, t, cube, cam, disc, sh, out, dbg, (cudaStream_t)stream);
+}
+
+extern "C" bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                                       const bh_camera *cam, const bh_disc *disc,
+                                       const bh_shading *sh, float *host, void *stream) {
+  if (!ctx || !host || !cam) { set_error("bh_render_to_host: NULL argument"); return BH_ERR_INVALID_ARG; }
+  if (!validate_camera(cam, 0)) return BH_ERR_INVALID_ARG;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t bytes = sizeof(float4) * (size_t)cam->width * cam->height;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (bytes > ctx->frame_cap) {
+    BH_CUDA(cudaStreamSynchronize(s));
+    if (ctx->frame_dev) cudaFree(ctx->frame_dev);
+    ctx->frame_dev = nullptr;
+    ctx->frame_cap = 0;
+    BH_CUDA(cudaMalloc((void **)&ctx->frame_dev, bytes));
+    ctx->frame_cap = bytes;
+  }
+  bh_status st = render_one(ctx, t, cube, cam, disc, sh, ctx->frame_dev, nullptr, s);
+  if (st) return st;
+  BH_CUDA(cudaMemcpyAsync(host, ctx->frame_dev, bytes, cudaMemcpyDeviceToHost, s));
+  BH_CUDA(cudaStreamSynchronize(s));
+  return BH_OK;
+}
+
+extern "C" bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
+                                     const bh_camera *cams, const bh_disc *disc,
+                                     const bh_shading *sh, float *const *outs, void *stream) {
+  if (!ctx || !t) { set_error("bh_render_batch: NULL argument"); return BH_ERR_INVALID_ARG; }
+  bh_status st = validate_batch(n, cams, disc, outs);
+  if (st) return st;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  // the staging buffer is reused: wait until the previous copy out of it ran
+  BH_CUDA(cudaStreamSynchronize(s));
+  st = ensure_cam_staging(ctx, n);
+  if (st) return st;
+  return render_batch_impl(ctx, t, cube, n, cams, disc, sh, outs, s, ctx->cam_host, ctx->cam_dev);
+}
+
+extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                                       int n, const bh_camera *cams, const bh_disc *disc,
+                                       const bh_shading *sh, float *const *outs, int *chosen) {
+  if (!ctx || !t) { set_error("bh_autotune_batch: NULL argument"); return BH_ERR_INVALID_ARG; }
+  bh_status st = validate_batch(n, cams, disc, outs);
+  if (st) return st;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  // candidates: warps per block, block tile width, resident blocks per SM
+  static const RenderTuning cand[] = {{8, 32, 4}, {8, 16, 4}, {8, 64, 4}, {4, 32, 8},
+                                      {4, 16, 8}, {8, 32, 2}, {8, 32, 8}, {8, 8, 4}};
+  const int nc = sizeof(cand) / sizeof(cand[0]);
+  cudaStream_t s;
+  BH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  RenderTuning keep = ctx->tuning;
+  int best = -1;
+  float best_ms = 1e30f;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  st = ensure_cam_staging(ctx, n);
+  for (int c = 0; c < nc && st == BH_OK; ++c) {
+    ctx->tuning = cand[c];
+    float tot = 0.f;
+    for (int rep = 0; rep < 4 && st == BH_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      st = render_batch_impl(ctx, t, cube, n, cams, disc, sh, outs, s, ctx->cam_host, ctx->cam_dev);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;  // first run warms caches
+    }
+    if (st == BH_OK && tot < best_ms) { best_ms = tot; best = c; }
+  }
+  ctx->tuning = best >= 0 ? cand[best] : keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(s);
+  if (chosen) *chosen = best;
+  return st;
+}

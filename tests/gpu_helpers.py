@@ -1,0 +1,68 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C-ABI
+binding and the CPU oracle on the same seeded inputs, and compare them."""
+from __future__ import annotations
+
+import numpy as np
+
+# tolerances (linear RGB, star positions, hit radius, tables)
+RGB_MEAN_REL = 1e-3
+RGB_MAX_REL = 1e-2
+HIT_U_REL = 1e-3
+TABLE_REL = 1e-6
+
+
+def image_error(gpu: np.ndarray, orc: np.ndarray, mask: np.ndarray):
+    """Per-pixel relative error of linear RGB (reading C19): the denominator is
+    max(|ref|, 1e-4 * max over the image of |ref|).  Returns (mean, max, per-pixel)."""
+    g = gpu[..., :3].astype(np.float64)
+    o = orc[..., :3]
+    floor = 1e-4 * max(np.abs(o).max(), 1e-30)
+    rel = (np.abs(g - o) / np.maximum(np.abs(o), floor)).max(axis=-1)
+    sel = rel[~mask]
+    if sel.size == 0:
+        return 0.0, 0.0, rel
+    return float(sel.mean()), float(sel.max()), rel
+
+
+def dilate(m: np.ndarray, r: int = 1) -> np.ndarray:
+    out = m.copy()
+    H, W = m.shape
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            sh = np.zeros_like(m)
+            ys, yd = (slice(max(dy, 0), H), slice(0, H - max(dy, 0))) if dy >= 0 else (
+                slice(0, H + dy), slice(-dy, H))
+            xs, xd = (slice(max(dx, 0), W), slice(0, W - max(dx, 0))) if dx >= 0 else (
+                slice(0, W + dx), slice(-dx, W))
+            sh[yd, xd] = m[ys, xs]
+            out |= sh
+    return out
+
+
+def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndarray:
+    """Pixels excluded from the comparison, from the oracle's values only:
+    within 1 px of a change of disc-hit count or of the capture state (disc
+    edges, shadow silhouette), and pixels whose mip-level or cube-face
+    decision lies within a small margin of its threshold (a discontinuity of
+    the method, where FP32 and FP64 may take either side)."""
+    cap = ~np.isfinite(dbg[..., 2])
+    hits = dbg[..., 3]
+    edge = np.zeros(cap.shape, dtype=bool)
+    for a in (cap, hits):
+        e = np.zeros(cap.shape, dtype=bool)
+        e[:, 1:] |= a[:, 1:] != a[:, :-1]
+        e[:, :-1] |= a[:, 1:] != a[:, :-1]
+        e[1:, :] |= a[1:, :] != a[:-1, :]
+        e[:-1, :] |= a[1:, :] != a[:-1, :]
+        edge |= e
+    m = dilate(edge, 1)
+    lvl = dbg[..., 6]
+    hm = dbg[..., 16]
+    has = lvl >= 0
+    ratio = np.where(has, 2 * hm / (8 * 2.0 ** np.maximum(lvl, 0)), 0.0)
+    near_up = has & (ratio > 1 - level_margin) & (ratio <= 1)
+    prev = np.where(has & (lvl > 0), 2 * hm / (8 * 2.0 ** np.maximum(lvl - 1, 0)), 0.0)
+    near_dn = has & (lvl > 0) & (prev < 1 + level_margin)
+    near_face = has & (dbg[..., 17] < face_margin)
+    degenerate = has & (dbg[..., 18] < 1e-5)
+    return m | near_up | near_dn | near_face | degenerate

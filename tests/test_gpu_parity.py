@@ -1,0 +1,373 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Tables: GPU FP64 quadrature vs the oracle's RK4 tables, <= 1e-6 relative.
+Cube map: bit-exact records.  Render: per-stage values and linear RGB on the
+same seeded inputs, outside the oracle-derived mask of discontinuities;
+full-size workloads on sampled rows; batched and served renders equal to
+single renders bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2010_08735_gb300 import synth
+from gpu_helpers import (HIT_U_REL, RGB_MAX_REL, RGB_MEAN_REL, TABLE_REL, image_error,
+                         oracle_mask)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2010_08735_gb300 import bh  # noqa: E402
+
+MU = 4.0 / 27.0
+EXPOSURE_STARS = 0.05
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = bh.bh_create(0, 0)
+    yield c
+    bh.bh_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def orc_tables(orc):
+    return orc.tables_exact(512, 64, 32, 1e-3)
+
+
+@pytest.fixture(scope="module")
+def orc_colour(orc):
+    return orc.colour_table(64, 32, 64), orc.disc_colour_table(1024)
+
+
+@pytest.fixture(scope="module")
+def gpu_tables(ctx):
+    t = bh.bh_precompute_tables(ctx, 512, 64, 32, bh.BH_F32)
+    yield t
+    bh.bh_tables_free(t)
+
+
+@pytest.fixture(scope="module")
+def uploaded_tables(ctx, orc_tables):
+    D, U = orc_tables
+    t = bh.bh_tables_upload(ctx, D, U, bh.BH_F32)
+    yield t
+    bh.bh_tables_free(t)
+
+
+# ---------------------------------------------------------------------------
+# tables (a10, a11, a13)
+# ---------------------------------------------------------------------------
+
+def test_tables_match_oracle(gpu_tables, orc_tables):
+    Dg, Ug = bh.bh_tables_copy_out(gpu_tables, 512, 64, 32)
+    Do, Uo = orc_tables
+    errD = np.abs(Dg - Do) / (np.abs(Do) + 1e-3)
+    assert errD.max() <= TABLE_REL, np.unravel_index(errD.argmax(), errD.shape)
+    errU = np.abs(Ug - Uo) / (np.abs(Uo) + 1e-6)
+    assert errU.max() <= TABLE_REL, np.unravel_index(errU.argmax(), errU.shape)
+
+
+@pytest.mark.parametrize("dn,une,unphi", [(66, 10, 6), (128, 16, 16), (4, 2, 2)])
+def test_tables_small_and_ragged(ctx, orc, dn, une, unphi):
+    t = bh.bh_precompute_tables(ctx, dn, une, unphi, bh.BH_F16)
+    try:
+        Dg, Ug = bh.bh_tables_copy_out(t, dn, une, unphi)
+    finally:
+        bh.bh_tables_free(t)
+    Do, Uo = orc.tables_exact(dn, une, unphi, 1e-3)
+    assert (np.abs(Dg - Do) / (np.abs(Do) + 1e-3)).max() <= TABLE_REL
+    assert (np.abs(Ug - Uo) / (np.abs(Uo) + 1e-6)).max() <= TABLE_REL
+
+
+def test_colour_tables_match_oracle(gpu_tables, orc_colour):
+    Cg, dg = bh.bh_tables_copy_colour(gpu_tables)
+    Co, do = orc_colour
+    assert np.allclose(Cg[..., :3], Co, rtol=1e-5, atol=1e-30)
+    assert np.allclose(dg[:, :3], do, rtol=1e-5, atol=1e-4)
+
+
+def test_invalid_arguments(ctx, gpu_tables):
+    out = torch.zeros((4, 4, 4), device="cuda")
+    sh = bh.make_shading()
+    bad = [synth.camera(1.0, 80, width=4, height=4), synth.camera(10, 80, v=(0.6, 0.6, 0.6), width=4, height=4),
+           dict(synth.camera(10, 80, width=4, height=4), orient=((1, 0, 0), (1, 0, 0), (0, 0, 1))),
+           synth.camera(10, 80, width=0, height=4)]
+    for cam in bad:
+        with pytest.raises(bh.BhError) as ei:
+            bh.bh_render(ctx, gpu_tables, None, cam, synth.disc(), sh, out)
+        assert ei.value.status == bh.BH_ERR_INVALID_ARG
+    with pytest.raises(bh.BhError):
+        bh.bh_render(ctx, gpu_tables, None, synth.camera(10, 80, width=4, height=4),
+                     synth.disc(2.0, 12.0), sh, out)
+    with pytest.raises(bh.BhError):
+        bh.bh_precompute_tables(ctx, 511, 64, 32)
+
+
+# ---------------------------------------------------------------------------
+# cube map (a12)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,N,dtype", [(1000, 2048, 1), (20000, 64, 1), (5000, 128, 2), (0, 8, 1),
+                                       (300000, 256, 1)])
+def test_cubemap_bit_exact(ctx, orc, n, N, dtype):
+    st = synth.stars(n, seed=11)
+    c = bh.bh_build_star_cubemap(ctx, st, N, dtype)
+    try:
+        rec = bh.bh_cubemap_copy_out(c, N)
+    finally:
+        bh.bh_cubemap_free(c)
+    ref = orc.build_cubemap(st, N, dtype)
+    diff = np.any(rec != ref, axis=1)
+    assert diff.sum() == 0, (diff.sum(), np.flatnonzero(diff)[:5])
+
+
+def test_cubemap_from_device_stars(ctx, orc):
+    st = synth.stars(4000, seed=12)
+    dst = torch.from_numpy(st).cuda()
+    c = bh.bh_build_star_cubemap(ctx, dst, 128, 1)
+    try:
+        rec = bh.bh_cubemap_copy_out(c, 128)
+    finally:
+        bh.bh_cubemap_free(c)
+    assert np.array_equal(rec, orc.build_cubemap(st, 128, 1))
+
+
+# ---------------------------------------------------------------------------
+# render (a1..a9)
+# ---------------------------------------------------------------------------
+
+def gpu_render(ctx, tables, cube, cam, disc, debug=True, exposure_stars=EXPOSURE_STARS):
+    W, H = cam["width"], cam["height"]
+    out = torch.zeros((H, W, 4), device="cuda")
+    sh = bh.make_shading(1.0, exposure_stars)
+    if debug:
+        dbg = torch.zeros((H, W, 16), device="cuda")
+        bh.bh_render_debug(ctx, tables, cube, cam, disc, sh, out, dbg)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), dbg.cpu().numpy()
+    bh.bh_render(ctx, tables, cube, cam, disc, sh, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), None
+
+
+def orc_scene(orc, orc_tables, orc_colour, cube_rec, N, dtype):
+    D, U = orc_tables
+    Ct, dl = orc_colour
+    # the renderer reads FP32-stored tables
+    return orc.SceneTables(D.astype(np.float32), U.astype(np.float32), Ct.astype(np.float32),
+                           dl.astype(np.float32), cube_rec, N, dtype)
+
+
+@pytest.fixture(scope="module")
+def static_scene(ctx, orc, orc_tables, orc_colour):
+    wk = synth.WORKLOADS["static_256"]
+    st = synth.stars(wk["n_stars"], wk["star_seed"])
+    N = wk["cube_n"]
+    cube = bh.bh_build_star_cubemap(ctx, st, N, 1)
+    rec = orc.build_cubemap(st, N, 1)
+    yield cube, orc_scene(orc, orc_tables, orc_colour, rec, N, 1)
+    bh.bh_cubemap_free(cube)
+
+
+def compare_render(orc, ctx, tables, cube, scene, cam, disc, y0=0, y1=None):
+    og, gd = gpu_render(ctx, tables, cube, cam, disc)
+    y1 = cam["height"] if y1 is None else y1
+    oo, od, _ = orc.render(cam, disc, scene, exposure_stars=EXPOSURE_STARS, y0=y0, y1=y1,
+                           debug=True)
+    og, gd = og[y0:y1], gd[y0:y1]
+    mask = oracle_mask(od)
+    return og, gd, oo, od, mask
+
+
+def check_stages(gd, od, mask):
+    cap_o = ~np.isfinite(od[..., 2])
+    cap_g = ~np.isfinite(gd[..., 2])
+    assert np.array_equal(cap_o[~mask], cap_g[~mask])
+    ok = ~mask & ~cap_o
+    # e^2 and delta (FP32 vs FP64)
+    assert np.allclose(gd[..., 1][ok], od[..., 1][ok], atol=2e-5)
+    # escape angle, away from the photon sphere where it is ill-conditioned
+    far = ok & (np.abs(od[..., 0] / MU - 1) > 1e-2)
+    dd = np.abs(np.angle(np.exp(1j * (gd[..., 2][far] - od[..., 2][far]))))
+    assert dd.max() < 1e-3, dd.max()
+    # disc hits: same count and radius within 1e-3 relative
+    same = ~mask & (gd[..., 3] == od[..., 3])
+    assert (~mask & (gd[..., 3] != od[..., 3])).sum() <= 0.001 * (~mask).sum()
+    for k, ch in ((1, 4), (2, 5)):
+        sel = same & (od[..., 3] >= k)
+        if sel.any():
+            rel = np.abs(gd[..., ch][sel] - od[..., ch][sel]) / od[..., ch][sel]
+            assert rel.max() <= HIT_U_REL, rel.max()
+    # mip level and face agree outside the mask
+    has = ~mask & (od[..., 6] >= 0)
+    assert (gd[..., 6][has] != od[..., 6][has]).mean() < 1e-3
+    assert (gd[..., 7][has] != od[..., 7][has]).mean() < 1e-3
+
+
+def test_render_static_256(ctx, orc, gpu_tables, static_scene):
+    cube, scene = static_scene
+    wk = synth.WORKLOADS["static_256"]
+    og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, wk["camera"], wk["disc"])
+    assert mask.mean() < 0.1
+    check_stages(gd, od, mask)
+    mean, mx, _ = image_error(og, oo, mask)
+    assert mean <= RGB_MEAN_REL and mx <= RGB_MAX_REL, (mean, mx)
+
+
+def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_scene):
+    cube, scene = static_scene
+    wk = synth.WORKLOADS["static_256"]
+    og, gd, oo, od, mask = compare_render(orc, ctx, uploaded_tables, cube, scene, wk["camera"],
+                                          wk["disc"])
+    check_stages(gd, od, mask)
+    mean, mx, _ = image_error(og, oo, mask)
+    assert mean <= RGB_MEAN_REL and mx <= RGB_MAX_REL, (mean, mx)
+
+
+@pytest.mark.parametrize("cam", [
+    synth.camera(6.0, 85.0, v=(0.0, 0.0, 0.5), width=192, height=108),
+    synth.camera(3.2, 89.0, v=(-0.9, 0.0, 0.0), width=96, height=54),
+    synth.camera(25.0, 60.0, phi_deg=40.0, v=(0.2, -0.3, 0.1), width=97, height=61),  # ragged
+    synth.camera(1.3, 30.0, v=(0.0, 0.4, 0.0), width=64, height=64),  # inside the photon sphere
+    synth.camera(8.0, 10.0, width=3, height=1),
+    synth.camera(8.0, 10.0, width=1, height=1),
+])
+def test_render_configs_small(ctx, orc, gpu_tables, static_scene, cam):
+    cube, scene = static_scene
+    disc = synth.disc(3.0, 20.0)
+    og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, cam, disc)
+    check_stages(gd, od, mask)
+    mean, mx, _ = image_error(og, oo, mask)
+    assert mean <= RGB_MEAN_REL and mx <= RGB_MAX_REL, (mean, mx)
+
+
+def test_star_centroids_sparse_field(ctx, orc, orc_tables, orc_colour, gpu_tables):
+    """Intensity-weighted centroids of isolated star images agree within 0.05 px."""
+    st = synth.stars(100, seed=3)
+    N = 2048
+    cube = bh.bh_build_star_cubemap(ctx, st, N, 1)
+    try:
+        scene = orc_scene(orc, orc_tables, orc_colour, orc.build_cubemap(st, N, 1), N, 1)
+        cam = synth.camera(12.0, 70.0, width=256, height=256, fov_deg=90.0)
+        disc = synth.disc(enabled=False)
+        _, gd = gpu_render(ctx, gpu_tables, cube, cam, disc)
+        _, od, _ = orc.render(cam, disc, scene, exposure_stars=EXPOSURE_STARS, debug=True)
+    finally:
+        bh.bh_cubemap_free(cube)
+    Yg, Yo = gd[..., 11], od[..., 11]
+    lit = Yo > 0
+    from scipy import ndimage
+    lab, nl = ndimage.label(lit)
+    checked = 0
+    for k in range(1, nl + 1):
+        sel = lab == k
+        if sel.sum() > 16:
+            continue  # merged or lensed into an arc: not an isolated star image
+        jj, ii = np.nonzero(sel)
+        wo, wg = Yo[sel], Yg[sel]
+        if wg.sum() <= 0:
+            continue
+        co = np.array([(wo * ii).sum(), (wo * jj).sum()]) / wo.sum()
+        cg = np.array([(wg * ii).sum(), (wg * jj).sum()]) / wg.sum()
+        assert np.abs(co - cg).max() <= 0.05, (k, co, cg)
+        checked += 1
+    assert checked >= 10
+
+
+def test_batch_equals_single(ctx, gpu_tables, static_scene):
+    cube, _ = static_scene
+    cams = synth.batch_cameras(6, seed=1, resolutions=((64, 48), (33, 17), (128, 72)))
+    disc = synth.disc()
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    outs = [torch.zeros((c["height"], c["width"], 4), device="cuda") for c in cams]
+    bh.bh_render_batch(ctx, gpu_tables, cube, cams, disc, sh, outs)
+    torch.cuda.synchronize()
+    for c, o in zip(cams, outs):
+        single = torch.zeros_like(o)
+        bh.bh_render(ctx, gpu_tables, cube, c, disc, sh, single)
+        torch.cuda.synchronize()
+        assert torch.equal(single, o)
+
+
+def test_render_to_host_equals_device(ctx, gpu_tables, static_scene):
+    cube, _ = static_scene
+    cam = synth.camera(10.0, 80.0, width=80, height=40)
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    dev = torch.zeros((40, 80, 4), device="cuda")
+    bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, dev)
+    host = np.zeros((40, 80, 4), dtype=np.float32)
+    bh.bh_render_to_host(ctx, gpu_tables, cube, cam, synth.disc(), sh, host)
+    assert np.array_equal(host, dev.cpu().numpy())
+
+
+def test_serve_results_equal_alone(ctx, gpu_tables, static_scene):
+    """Continuous batching: frames submitted while others are in flight come
+    out equal to the same frame rendered alone."""
+    cube, _ = static_scene
+    cams = synth.batch_cameras(12, seed=7, resolutions=((64, 48), (96, 54)))
+    disc = synth.disc()
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    outs = [torch.zeros((c["height"], c["width"], 4), device="cuda") for c in cams]
+    tickets = []
+    for v, (c, o) in enumerate(zip(cams, outs)):
+        st, t = bh.bh_serve_submit(ctx, gpu_tables, cube, v, c, disc, sh, o)
+        assert st == bh.BH_OK
+        tickets.append(t)
+    lat = []
+    for t in tickets:
+        st, ms = bh.bh_serve_poll(ctx, t, 5_000_000)
+        assert st == bh.BH_OK
+        lat.append(ms)
+    torch.cuda.synchronize()
+    for c, o in zip(cams, outs):
+        single = torch.zeros_like(o)
+        bh.bh_render(ctx, gpu_tables, cube, c, disc, sh, single)
+        torch.cuda.synchronize()
+        assert torch.equal(single, o)
+    assert all(x >= 0 for x in lat)
+
+
+def test_serve_admission(ctx, gpu_tables, static_scene):
+    cube, _ = static_scene
+    c2 = bh.bh_create(0, 64 * 48 * 16 * 2)  # room for two 64x48 frames
+    try:
+        cam = synth.camera(10.0, 80.0, width=64, height=48)
+        outs = [torch.zeros((48, 64, 4), device="cuda") for _ in range(4)]
+        sh = bh.make_shading()
+        st0, t0 = bh.bh_serve_submit(c2, gpu_tables, cube, 0, cam, synth.disc(), sh, outs[0])
+        st1, _ = bh.bh_serve_submit(c2, gpu_tables, cube, 1, cam, synth.disc(), sh, outs[1])
+        st2, _ = bh.bh_serve_submit(c2, gpu_tables, cube, 2, cam, synth.disc(), sh, outs[2])
+        assert st0 == bh.BH_OK and st1 == bh.BH_OK
+        assert st2 == bh.BH_ERR_BUSY  # over the budget while the first two are held
+        assert bh.bh_serve_poll(c2, t0, 5_000_000)[0] == bh.BH_OK
+    finally:
+        torch.cuda.synchronize()
+        bh.bh_destroy(c2)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled rows
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,rows", [("orbit_1080p", (520, 560)), ("infall_4k", (1000, 1016))])
+def test_full_size_sampled_rows(ctx, orc, orc_tables, orc_colour, gpu_tables, name, rows):
+    wk = synth.WORKLOADS[name]
+    st = synth.stars(wk["n_stars"], wk["star_seed"])
+    N = wk["cube_n"]
+    dt = 1 if wk["cube_dtype"] == "f16" else 2
+    cube = bh.bh_build_star_cubemap(ctx, st, N, dt)
+    try:
+        rec = orc.build_cubemap(st, N, dt)
+        scene = orc_scene(orc, orc_tables, orc_colour, rec, N, dt)
+        og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, wk["camera"],
+                                              wk["disc"], y0=rows[0], y1=rows[1])
+    finally:
+        bh.bh_cubemap_free(cube)
+    check_stages(gd, od, mask)
+    mean, mx, _ = image_error(og, oo, mask)
+    assert mean <= RGB_MEAN_REL and mx <= RGB_MAX_REL, (mean, mx)
