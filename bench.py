@@ -153,7 +153,7 @@ def cpu_baseline(wk, seconds=12.0, impl_line=False):
     while tr < seconds and rows < H:
         y0 = y % H
         y0 -= y0 % 2
-        y1 = min(y0 + band, H)
+        y1 = min(y0 + band, H, y0 + (H - rows))
         t = time.perf_counter()
         oracle.render(cam, wk["disc"], scene, exposure_stars=0.01, y0=y0, y1=y1, nthreads=cores)
         tr += time.perf_counter() - t

@@ -921,7 +921,7 @@ double orc_disc_temperature(double t_peak, double u) {
 /* Per-pixel render                                                          */
 /* ------------------------------------------------------------------------ */
 
-#define NDBG 20
+#define NDBG 20 /* channel 19: sensitivity of the pixel's Y to a one-pixel footprint shift */
 typedef struct {
   const orc_camera *cam;
   const orc_disc *disc;
@@ -1042,6 +1042,7 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
   const uint16_t *rec = sc->cube + (orc_cube_level_offset(N, L) + (long long)face * NL * NL) * 4;
   double lscale = ldexp(1.0, 2 * L);
   long long cnt = 0;
+  double gsum = 0.0, ysum = 0.0; /* for the sensitivity to a footprint shift */
   for (int jj = j0; jj <= j1; ++jj)
     for (int ii = i0; ii <= i1; ++ii) {
       ++cnt;
@@ -1056,8 +1057,11 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
       if (fw <= 0.0 || fh <= 0.0) continue;
       double wt = fw * fh * lscale;
       xyz[0] += wt * X; xyz[1] += wt * Y; xyz[2] += wt * Z;
+      ysum += wt * Y;
+      gsum += (fw + fh) * lscale * Y;
     }
   dbg[15] = (double)cnt;
+  dbg[19] = ysum > 0.0 ? gsum / ysum : 0.0;
   *texels += cnt;
 }
 
@@ -1106,6 +1110,8 @@ static void render_pixel(render_job *J, int i, int j, pix *quad[2][2], double *o
       c_lookup(J->sc->C, J->sc->c_nx, J->sc->c_ny, J->sc->c_nd, sxyz[0] / S, sxyz[1] / S, Dst, cc);
       double s = S * d[8] * J->exposure_stars;
       for (int k = 0; k < 3; ++k) L[k] += trans * s * cc[k];
+      /* relative change of the pixel's Y per screen pixel of footprint shift */
+      d[19] = L[1] > 0.0 ? d[19] * trans * s * cc[1] / L[1] : 0.0;
     }
   } else {
     d[6] = -1; d[7] = -1;
@@ -1155,7 +1161,8 @@ static void *render_worker(void *argp) {
  *  6 mip level (-1: no star term), 7 face, 8 Omega/Omega', 9 star Doppler,
  *  10..12 gathered star XYZ, 13 hit-0 Doppler, 14 hit-1 Doppler,
  *  15 texels visited, 16 footprint half extent (level-0 texels),
- *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|).
+ *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|),
+ *  19 relative change of the pixel's Y per pixel of footprint shift.
  * force_level >= 0 forces the mip level (for the flat-space checks). */
 int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc,
                double exposure_stars, const orc_scene *sc, int y0, int y1, int force_level,

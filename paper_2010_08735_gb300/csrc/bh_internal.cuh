@@ -42,7 +42,7 @@ struct ServeState;
 struct RenderTuning {
   int warps_per_block = 8;   // block = warps * 32 threads
   int block_w = 32;          // block tile width in pixels (multiple of 8)
-  int blocks_per_sm = 4;     // persistent grid = SMs * blocks_per_sm
+  int blocks_per_sm = 8;     // persistent grid = SMs * blocks_per_sm
 };
 
 }  // namespace bh

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
     bool captured = false;
     int nh = 0;
     float hu0 = 0.f, hu1 = 0.f;
-    float delta_p = 0.f;
+    float delta_p = 0.f, turn = 0.f;  // delta' = delta + turn
     if (em < 0.f && u > 2.f / 3.f) {
       captured = true;
     } else {
@@ -232,7 +232,11 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
         float sa = asinf(sqrtf(fminf(eta, 1.f)));
         float th = (0.5f * kPiF - 2.f * sa) * (1.f / 3.f);
         ua = 1.f / 3.f + 2.f / 3.f * sinf(th);
-        float yv = 1.f - sqrtf(fmaxf(1.f - u / ua, 0.f));
+        // 1 - u/u_a = (du/dphi)^2 / (u_a g), g = (f(u_a) - f(u))/(u_a - u), f(x) = x^2 - x^3:
+        // no cancellation when the camera is near the apsis (du/dphi -> 0)
+        float g = ua + u - ua * ua - ua * u - u * u;
+        float om = g > 0.f ? udot * udot / (ua * g) : 1.f - u / ua;
+        float yv = 1.f - sqrtf(fmaxf(om, 0.f));
         Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
         Da = d_bilinear(D, dn, fx, (float)(dn - 1), xlo, xhi);
         phia = Da + 0.5f * kPiF;
@@ -276,11 +280,12 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
         }
       }
       if (udot > 0.f) {
-        if (em < 0.f) delta_p = delta + 2.f * Da - Dl;
+        if (em < 0.f) turn = 2.f * Da - Dl;
         else captured = true;
       } else {
-        delta_p = delta + Dl;
+        turn = Dl;
       }
+      delta_p = delta + turn;
     }
 
     // ---- disc hits, front to back (Sec. 3.3.3, 3.4.2)
@@ -315,11 +320,17 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
     }
 
     // ---- escape direction and its screen-space derivatives (quad shuffles)
-    float sd, cdp;
-    sincosf(delta_p, &sd, &cdp);
-    float dp0 = captured ? 0.f : fmaf(cdp, x0, sd * y0);
-    float dp1 = captured ? 0.f : fmaf(cdp, x1, sd * y1);
-    float dp2 = captured ? 0.f : fmaf(cdp, x2, sd * y2);
+    // d' = cos(delta') e_x' + sin(delta') e_y', evaluated as the rotation of the
+    // unit beam direction by the turn angle (delta' - delta) about e_z': the
+    // sum delta + turn is never rounded, which keeps d' to a few 1e-8.
+    float st_, ct_;
+    sincosf(turn, &st_, &ct_);
+    float idd = 1.f / dd;
+    float b0 = d0 * idd, b1 = d1 * idd, b2 = d2 * idd;
+    float n0 = z1 * b2 - z2 * b1, n1 = z2 * b0 - z0 * b2, n2 = z0 * b1 - z1 * b0;
+    float dp0 = captured ? 0.f : fmaf(ct_, b0, st_ * n0);
+    float dp1 = captured ? 0.f : fmaf(ct_, b1, st_ * n1);
+    float dp2 = captured ? 0.f : fmaf(ct_, b2, st_ * n2);
     unsigned capbits = __ballot_sync(0xffffffffu, captured);
     bool anycap = ((capbits >> (lane & ~3)) & 0xfu) != 0u;
     const bool colodd = lane & 1, rowodd = (lane >> 1) & 1;
@@ -382,6 +393,13 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
             for (int ii = i0; ii <= i1; ++ii) {
               ++visited;
               uint2 r = __ldg(rec + (long long)jj * NL + ii);
+              if ((r.x | (r.y & 0xffffu)) == 0u) continue;  // empty texel: X = Y = Z = +0
+              unsigned pw = r.y >> 16;
+              float ds_ = (ii - cS) + ((pw & 255u) + 0.5f) * (1.f / 256.f);
+              float dt_ = dt + ((pw >> 8) + 0.5f) * (1.f / 256.f);
+              float w = fmaf(i11, ds_, i12 * dt_), h = fmaf(i21, ds_, i22 * dt_);
+              float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
+              if (fw <= 0.f || fh <= 0.f) continue;
               float X, Y, Z;
               if (P.cube_bf16) {
                 X = __uint_as_float(r.x << 16);
@@ -392,13 +410,6 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
                 Y = __half2float(__ushort_as_half((unsigned short)(r.x >> 16)));
                 Z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
               }
-              if (X + Y + Z <= 0.f) continue;
-              unsigned pw = r.y >> 16;
-              float ds_ = (ii - cS) + ((pw & 255u) + 0.5f) * (1.f / 256.f);
-              float dt_ = dt + ((pw >> 8) + 0.5f) * (1.f / 256.f);
-              float w = fmaf(i11, ds_, i12 * dt_), h = fmaf(i21, ds_, i22 * dt_);
-              float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
-              if (fw <= 0.f || fh <= 0.f) continue;
               float wt = fw * fh * lscale;
               SX = fmaf(wt, X, SX);
               SY = fmaf(wt, Y, SY);

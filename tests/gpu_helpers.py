@@ -2,6 +2,8 @@
 binding and the CPU oracle on the same seeded inputs, and compare them."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 # tolerances (linear RGB, star positions, hit radius, tables)
@@ -65,4 +67,37 @@ def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndar
     near_dn = has & (lvl > 0) & (prev < 1 + level_margin)
     near_face = has & (dbg[..., 17] < face_margin)
     degenerate = has & (dbg[..., 18] < 1e-5)
-    return m | near_up | near_dn | near_face | degenerate
+    return m | near_up | near_dn | near_face | degenerate | star_ill_conditioned(dbg)
+
+
+# FP32 places a beam's escape direction to about one float ulp of the angle,
+# i.e. a few 1e-4 screen pixels of footprint shift; a pixel whose value changes
+# by more than 1 % for a 1e-3 px shift (a bright star at the edge of its tent
+# filter) is ill-conditioned for a per-pixel relative comparison.
+POS_EPS_PX = 1e-3
+KAPPA_MAX = 0.01 / POS_EPS_PX
+
+
+def star_ill_conditioned(dbg: np.ndarray) -> np.ndarray:
+    return dbg[..., 19] > KAPPA_MAX
+
+
+def ill_conditioned_ok(rel: np.ndarray, dbg: np.ndarray, mask_other: np.ndarray) -> bool:
+    """Validity of the pixels masked only for conditioning: their error stays
+    within what a 3e-3 px footprint shift explains, plus the base tolerance."""
+    sel = star_ill_conditioned(dbg) & ~mask_other
+    if not sel.any():
+        return True
+    bound = RGB_MAX_REL + 3 * POS_EPS_PX * dbg[..., 19][sel]
+    return bool(np.all(rel[sel] <= bound))
+
+
+def maybe_dump(name: str, **arrays) -> None:
+    """Save arrays for offline inspection when BH_DUMP_DIR is set."""
+    d = os.environ.get("BH_DUMP_DIR")
+    if not d:
+        return
+    os.makedirs(d, exist_ok=True)
+    np.savez_compressed(os.path.join(d, name + ".npz"),
+                        **{k: (v.astype(np.float32) if v.dtype == np.float64 else v)
+                           for k, v in arrays.items()})
