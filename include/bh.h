@@ -136,6 +136,26 @@ bh_status bh_build_star_cubemap(bh_ctx *ctx, const bh_star *stars, long long n, 
                                 bh_dtype storage, int stars_on_device, void *stream,
                                 bh_cubemap **out);
 
+/* Allocation-free form of bh_build_star_cubemap, for callers that may not
+ * allocate device memory themselves (applications that give all device
+ * memory to their own pool or arena, real-time threads that must not call
+ * cudaMalloc/cudaFree because those can synchronise the device).  The paper
+ * has no counterpart; the records are the same as bh_build_star_cubemap's.
+ *  - stars_device: n stars in device memory; records_device: caller-owned
+ *    device buffer of bh_cubemap_records(face_size) x 4 uint16, 8-byte aligned.
+ *  - face_size: power of two, at most 128 (the size of the library's static
+ *    scratch array, about 6.9 MB, held on every GPU that loads the library
+ *    until the process exits); larger sizes return BH_ERR_INVALID_ARG.
+ *  - Works on the current CUDA device and needs no bh_ctx.  The first call on
+ *    a device looks up the scratch array's device address; make that first
+ *    call before any stream capture.
+ *  - Allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *    Every call shares the one scratch array, so calls whose work overlaps
+ *    on the GPU (other streams, other threads) race: serialise them.
+ *  - Enqueued on `stream`. */
+bh_status bh_build_star_cubemap_noalloc(const bh_star *stars_device, long long n, int face_size,
+                                        bh_dtype storage, uint16_t *records_device, void *stream);
+
 /* Number of texel records (all faces, all levels) of a cube map. */
 long long bh_cubemap_records(int face_size);
 

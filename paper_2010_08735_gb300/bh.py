@@ -77,6 +77,7 @@ def lib():
             "bh_build_star_cubemap": [_vp, _vp, C.c_longlong, C.c_int, C.c_int, C.c_int, _vp,
                                       P(_vp)],
             "bh_cubemap_copy_out": [_vp, P(C.c_uint16), C.c_longlong],
+            "bh_build_star_cubemap_noalloc": [_vp, C.c_longlong, C.c_int, C.c_int, _vp, _vp],
             "bh_render": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
             "bh_render_debug": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp, _vp],
             "bh_render_to_host": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
@@ -249,6 +250,17 @@ def bh_build_star_cubemap(ctx: int, stars, face_size: int, storage=BH_F16, strea
                                        C.byref(out)))
     del keep
     return out.value
+
+
+def bh_build_star_cubemap_noalloc(stars, face_size: int, storage, records, stream=None) -> None:
+    """Allocation-free cube-map build: stars is a (n, 5) float32 CUDA tensor,
+    records a caller-owned CUDA tensor of bh_cubemap_records(face_size) x 4
+    uint16 (or int16); face_size <= 128.  Runs on the current device."""
+    assert stars.is_cuda and stars.is_contiguous() and stars.shape[-1] == 5
+    assert records.is_cuda and records.numel() >= 4 * bh_cubemap_records(face_size)
+    _check(lib().bh_build_star_cubemap_noalloc(stars.data_ptr() if stars.shape[0] else None,
+                                               stars.shape[0], face_size, storage,
+                                               records.data_ptr(), _stream(stream)))
 
 
 def bh_cubemap_records(face_size: int) -> int:

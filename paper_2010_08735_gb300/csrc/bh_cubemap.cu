@@ -252,3 +252,96 @@ extern "C" void bh_cubemap_free(bh_cubemap *c) {
   cudaFree(c->rec);
   delete c;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free cube-map build
+//
+// For callers that may not allocate device memory themselves: applications
+// that hand every byte of device memory to their own pool or arena (engines,
+// plug-in hosts with a fixed memory budget), and real-time threads that must
+// not call cudaMalloc/cudaFree, which can synchronise the device and take an
+// unbounded time.  The scratch lives in one file-scope device array, sized for
+// faces of up to kNoAllocMaxFace texels; every GPU that loads this library
+// holds it (about 6.9 MB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace bh {
+
+constexpr int kNoAllocMaxFace = 128;
+constexpr long long kNoAllocTexels0 = 6LL * kNoAllocMaxFace * kNoAllocMaxFace;
+constexpr long long kNoAllocTexels1 = kNoAllocTexels0 / 4;
+// accumulators (5 x 64 bit per level-0 texel), level sums (3 x 64 bit per
+// texel of two consecutive levels), matching functions (3 x 95 doubles)
+constexpr size_t kNoAllocScratchWords = 5 * kNoAllocTexels0 + 3 * kNoAllocTexels0 + 3 * kNoAllocTexels1 + 3 * kNLambda;
+
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchWords];
+
+// Device address of the scratch array, looked up once per device with that
+// device current (the host-side name of a __device__ array is not a device
+// address).
+static bh_status noalloc_scratch(int device, unsigned long long **out) {
+  static std::mutex mu;
+  static unsigned long long *addr[64] = {nullptr};
+  if (device < 0 || device >= 64) {
+    set_error("bh_build_star_cubemap_noalloc: device %d out of range", device);
+    return BH_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "bh_build_star_cubemap_noalloc: cudaGetSymbolAddress");
+    addr[device] = static_cast<unsigned long long *>(p);
+  }
+  *out = addr[device];
+  return BH_OK;
+}
+
+}  // namespace bh
+
+extern "C" bh_status bh_build_star_cubemap_noalloc(const bh_star *stars_device, long long n,
+                                                   int N, bh_dtype storage, uint16_t *records_device,
+                                                   void *stream) {
+  if ((n > 0 && !stars_device) || !records_device) {
+    set_error("bh_build_star_cubemap_noalloc: NULL argument");
+    return BH_ERR_INVALID_ARG;
+  }
+  if (N < 1 || (N & (N - 1)) || N > kNoAllocMaxFace) {
+    set_error("bh_build_star_cubemap_noalloc: face_size %d must be a power of two <= %d (the size of "
+              "its static scratch)", N, kNoAllocMaxFace);
+    return BH_ERR_INVALID_ARG;
+  }
+  if (n < 0 || (storage != BH_F16 && storage != BH_BF16) || ((uintptr_t)records_device & 7)) {
+    set_error("bh_build_star_cubemap_noalloc: n >= 0, storage BH_F16/BH_BF16 and 8-byte aligned records required");
+    return BH_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  BH_CUDA(cudaGetDevice(&dev));
+  unsigned long long *scratch = nullptr;
+  bh_status st = noalloc_scratch(dev, &scratch);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  long long nt0 = 6LL * N * N;
+  unsigned long long *acc = scratch;
+  long long *sums0 = reinterpret_cast<long long *>(scratch + 5 * kNoAllocTexels0);
+  long long *sums1 = sums0 + 3 * kNoAllocTexels0;
+  double *cmf = reinterpret_cast<double *>(sums1 + 3 * kNoAllocTexels1);
+  uint2 *rec = reinterpret_cast<uint2 *>(records_device);
+  int levels = cube_levels(N);
+  // the array keeps the previous call's contents: the accumulators must start at zero
+  BH_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 5 * nt0, s));
+  cube_cmf_kernel<<<1, 128, 0, s>>>(cmf);
+  if (n > 0) star_bin_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(stars_device, n, N, cmf, acc);
+  level0_kernel<<<(unsigned)((nt0 + 255) / 256), 256, 0, s>>>(acc, nt0, storage, rec, sums0);
+  long long *ps = sums0, *cs = sums1;
+  for (int L = 1; L < levels; ++L) {
+    int Np = N >> (L - 1);
+    long long ntc = 6LL * (Np / 2) * (Np / 2);
+    mip_kernel<<<(unsigned)((ntc + 255) / 256), 256, 0, s>>>(ps, rec + cube_level_offset(N, L - 1), Np, L,
+                                                              storage, cs, rec + cube_level_offset(N, L));
+    long long *tmp = ps;
+    ps = cs;
+    cs = tmp;
+  }
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
+}
