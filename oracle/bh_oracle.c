@@ -1042,7 +1042,7 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
   const uint16_t *rec = sc->cube + (orc_cube_level_offset(N, L) + (long long)face * NL * NL) * 4;
   double lscale = ldexp(1.0, 2 * L);
   long long cnt = 0;
-  double gsum = 0.0, ysum = 0.0; /* for the sensitivity to a footprint shift */
+  double gw = 0.0, gh = 0.0, ysum = 0.0; /* for the sensitivity to a footprint shift */
   for (int jj = j0; jj <= j1; ++jj)
     for (int ii = i0; ii <= i1; ++ii) {
       ++cnt;
@@ -1058,10 +1058,11 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
       double wt = fw * fh * lscale;
       xyz[0] += wt * X; xyz[1] += wt * Y; xyz[2] += wt * Z;
       ysum += wt * Y;
-      gsum += (fw + fh) * lscale * Y;
+      gw += (w > 0.0 ? 1.0 : -1.0) * fh * lscale * Y; /* d/d(shift in w) of the Y sum */
+      gh += (h > 0.0 ? 1.0 : -1.0) * fw * lscale * Y;
     }
   dbg[15] = (double)cnt;
-  dbg[19] = ysum > 0.0 ? gsum / ysum : 0.0;
+  dbg[19] = ysum > 0.0 ? sqrt(gw * gw + gh * gh) / ysum : 0.0;
   *texels += cnt;
 }
 
@@ -1162,7 +1163,7 @@ static void *render_worker(void *argp) {
  *  10..12 gathered star XYZ, 13 hit-0 Doppler, 14 hit-1 Doppler,
  *  15 texels visited, 16 footprint half extent (level-0 texels),
  *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|),
- *  19 relative change of the pixel's Y per pixel of footprint shift.
+ *  19 |gradient| of the pixel's Y per pixel of footprint shift, relative to Y.
  * force_level >= 0 forces the mip level (for the flat-space checks). */
 int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc,
                double exposure_stars, const orc_scene *sc, int y0, int y1, int force_level,

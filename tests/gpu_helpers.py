@@ -70,10 +70,13 @@ def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndar
     return m | near_up | near_dn | near_face | degenerate | star_ill_conditioned(dbg)
 
 
-# FP32 places a beam's escape direction to about one float ulp of the angle,
-# i.e. a few 1e-4 screen pixels of footprint shift; a pixel whose value changes
-# by more than 1 % for a 1e-3 px shift (a bright star at the edge of its tent
-# filter) is ill-conditioned for a per-pixel relative comparison.
+# FP32 places a beam's escape direction to about one float ulp of the angle
+# (2.4e-7 rad near 2), i.e. up to about 1e-3 of a 4K pixel; a pixel whose value
+# changes by more than 1 % for a 1e-3 px shift of its footprint (a bright star
+# near the edge of its tent filter) is ill-conditioned for a per-pixel
+# relative comparison.  The oracle reports that sensitivity (|gradient of the
+# star sum| / star sum, per pixel of shift, scaled by the star share of the
+# pixel).
 POS_EPS_PX = 1e-3
 KAPPA_MAX = 0.01 / POS_EPS_PX
 
