@@ -277,6 +277,18 @@ def run_ours(args):
     # --- served (continuous batching) and batched forms on the same frames
     served = serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=max(32, args.steps))
     batched = batch_run(bh, ctx, tables, cube, sh, dev)
+    served_mixed = serve_workload(bh, dev, tables, cube, sh) if args.serve_workload else None
+    if served_mixed is not None:
+        # the largest per-viewer request rate whose p99 latency stays within two
+        # 60 Hz frame periods
+        sweep = []
+        for hz in (5.0, 10.0, 15.0, 20.0, 30.0):
+            r = serve_workload(bh, dev, tables, cube, sh, duration=0.6, rate_hz=hz)
+            sweep.append({"rate_hz": hz, "p99_ms": r["p99_ms"], "frames_per_s": r["frames_per_s"],
+                          "mpix_per_s": r["mpix_per_s"], "refused": r["refused"]})
+        ok = [x["rate_hz"] for x in sweep if x["p99_ms"] is not None and x["p99_ms"] <= 2000.0 / 60.0]
+        served_mixed["rate_sweep"] = sweep
+        served_mixed["max_rate_hz_p99_within_2_frames"] = max(ok) if ok else None
 
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -302,7 +314,7 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "precompute_ms": {"tables_D_U_colour": precompute_ms, "cubemap_1M_stars": cubemap_ms},
-        "served": served, "batched": batched,
+        "served": served, "batched": batched, "served_mixed": served_mixed,
     }
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wk, seconds=12.0)
@@ -347,6 +359,88 @@ def serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=64, viewers=16):
             "frames": frames, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
+def viewer_camera(v, t):
+    """Camera of a served viewer at time t: a circular orbit (moving along e_phi)
+    or a radial fall (moving along -e_r), from the viewer's seeded parameters."""
+    from paper_2010_08735_gb300 import synth
+    if v["kind"] == "circular":
+        r = v["r0"]
+        cam = synth.camera(r, v["theta"] / synth.DEG, v["phi0"] / synth.DEG + (v["speed"] / r) * t / synth.DEG,
+                           v=(0.0, 0.0, v["speed"]), width=v["width"], height=v["height"])
+    else:
+        r = max(2.0, v["r0"] - v["speed"] * t * 50.0)
+        cam = synth.camera(r, v["theta"] / synth.DEG, v["phi0"] / synth.DEG, v=(-v["speed"], 0.0, 0.0),
+                           width=v["width"], height=v["height"])
+    return cam
+
+
+def serve_workload(bh, dev, tables, cube, sh, duration=1.5, viewers=256, rate_hz=60.0,
+                   budget=40 << 30):
+    """The served workload: `viewers` viewers with Poisson frame requests at
+    rate_hz each (mixed 720p/1080p/4K), admission under a device-memory budget,
+    one disc-parameter change half way that switches new requests to freshly
+    rebuilt tables (frames queued on the old tables finish on them).  Open loop
+    in wall-clock time; reports completed frames/s, Mpix/s, p50/p99 latency and
+    the refused requests."""
+    import torch
+    from paper_2010_08735_gb300 import synth
+    tr = synth.viewer_traffic(viewers, seed=4, rate_hz=rate_hz, duration_s=duration)
+    ctx = bh.bh_create(dev.index or 0, budget)
+    vs = tr["viewers"]
+    bufs = [[torch.empty((v["height"], v["width"], 4), device=dev) for _ in range(2)] for v in vs]
+    disc_a, disc_b = synth.disc(3.0, 12.0), synth.disc(3.0, 14.0)
+    cur_tables, old_tables = tables, None
+    pending = {}   # ticket -> (viewer, pixels)
+    slot = [0] * len(vs)
+    lat, px_done, refused, submitted = [], 0, 0, 0
+    switched = False
+    t0 = time.perf_counter()
+    for te, vid in tr["events"]:
+        while time.perf_counter() - t0 < te:
+            for tk in list(pending):
+                st, ms = bh.bh_serve_poll(ctx, tk, 0)
+                if st == bh.BH_OK:
+                    lat.append(ms)
+                    px_done += pending.pop(tk)[1]
+        if not switched and te >= duration / 2:
+            old_tables = cur_tables
+            cur_tables = bh.bh_precompute_tables(ctx, 512, 64, 32, bh.BH_F32)
+            switched = True
+        v = vs[vid]
+        disc = disc_b if switched else disc_a
+        if sum(1 for p in pending.values() if p[0] == vid) >= 2:
+            refused += 1  # both of the viewer's frame buffers are still in use
+            continue
+        out = bufs[vid][slot[vid]]
+        st, tk = bh.bh_serve_submit(ctx, cur_tables, cube, vid, viewer_camera(v, te), disc, sh, out)
+        submitted += 1
+        if st == bh.BH_OK:
+            pending[tk] = (vid, v["width"] * v["height"])
+            slot[vid] ^= 1
+        else:
+            refused += 1
+    while pending:
+        for tk in list(pending):
+            st, ms = bh.bh_serve_poll(ctx, tk, 1000)
+            if st == bh.BH_OK:
+                lat.append(ms)
+                px_done += pending.pop(tk)[1]
+    el = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    if old_tables is not None and cur_tables is not tables:
+        bh.bh_tables_free(cur_tables)
+    bh.bh_destroy(ctx)
+    lat.sort()
+    n = len(lat)
+    return {"viewers": viewers, "rate_hz_per_viewer": rate_hz, "duration_s": el,
+            "offered_req_per_s": len(tr["events"]) / duration, "submitted": submitted,
+            "refused": refused, "completed": n, "frames_per_s": n / el,
+            "mpix_per_s": px_done / 1e6 / el, "frames_1080p_equiv_per_s": px_done / (1920 * 1080) / el,
+            "p50_ms": lat[n // 2] if n else None, "p99_ms": lat[min(n - 1, int(0.99 * n))] if n else None,
+            "table_rebuilds": 1, "budget_bytes": budget,
+            "mix": "720p/1080p/4K uniform; circular or radial trajectories"}
+
+
 def batch_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
     """64 cameras of mixed resolution in one persistent launch; Mpix/s and
     1080p-equivalent frames/s, after the autotuner picked a tile shape."""
@@ -379,6 +473,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-serve-workload", dest="serve_workload", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -107,8 +107,8 @@ bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, const double 
 bh_status bh_tables_copy_out(const bh_tables *t, double *D_host, double *U_host);
 
 /* Copy the colour tables: C as [log2 D][y][x] float4 (XYZ, pad), 64*32*64*4
- * floats; the disc table as 1024 float4 (ln X, ln Y, ln Z, pad).  Either may
- * be NULL.  Synchronises. */
+ * floats; the disc black-body table as 1024 float4 (ln Y, X/Y, Z/Y, pad) at
+ * log2 T = 8 + 12 (k + 1/2)/1024.  Either may be NULL.  Synchronises. */
 bh_status bh_tables_copy_colour(const bh_tables *t, float *C_host, float *disc_host);
 void bh_tables_free(bh_tables *t);
 

@@ -30,7 +30,7 @@ SRC = HERE / "bh_oracle.c"
 LIB = HERE / "liboracle.so"
 
 MU = 4.0 / 27.0
-NDBG = 20
+NDBG = 23
 
 _lib = None
 

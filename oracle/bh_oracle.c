@@ -425,21 +425,21 @@ void orc_xyz_to_rgb_matrix(double *m) {
     for (int c = 0; c < 3; ++c) m[r * 3 + c] = I[r * 3 + c] / S[r];
 }
 
-/* Disc colour table: ln X, ln Y, ln Z of B_T at log2 T = 8 + 12 (k+1/2)/n. */
+/* Disc colour table: ln Y, X/Y and Z/Y of B_T at log2 T = 8 + 12 (k+1/2)/n. */
 int orc_disc_colour_table(int n, double *out) {
   for (int k = 0; k < n; ++k) {
     double T = exp2(8.0 + 12.0 * (k + 0.5) / n);
     double xyz[3];
     orc_blackbody_xyz(T, xyz);
-    out[3 * k + 0] = log(xyz[0]);
-    out[3 * k + 1] = log(xyz[1]);
-    out[3 * k + 2] = log(xyz[2]);
+    out[3 * k + 0] = log(xyz[1]);
+    out[3 * k + 1] = xyz[0] / xyz[1];
+    out[3 * k + 2] = xyz[2] / xyz[1];
   }
   return 0;
 }
 
-/* XYZ of B_T from the disc colour table: linear in log2 T of ln XYZ, clamped
- * to the table's range; 0 below 2^8 K. */
+/* XYZ of B_T from the disc colour table: ln Y, X/Y and Z/Y linear in log2 T,
+ * clamped to the table's range; 0 below 2^8 K. */
 static void disc_xyz(const double *tab, int n, double T, double *xyz) {
   if (!(T >= 256.0)) { xyz[0] = xyz[1] = xyz[2] = 0.0; return; }
   double f = (log2(T) - 8.0) / 12.0 * n - 0.5;
@@ -448,7 +448,10 @@ static void disc_xyz(const double *tab, int n, double T, double *xyz) {
   int k0 = (int)floor(f);
   int k1 = k0 + 1 > n - 1 ? n - 1 : k0 + 1;
   double t = f - k0;
-  for (int c = 0; c < 3; ++c) xyz[c] = exp(lerp(tab[3 * k0 + c], tab[3 * k1 + c], t));
+  double Y = exp(lerp(tab[3 * k0], tab[3 * k1], t));
+  xyz[0] = Y * lerp(tab[3 * k0 + 1], tab[3 * k1 + 1], t);
+  xyz[1] = Y;
+  xyz[2] = Y * lerp(tab[3 * k0 + 2], tab[3 * k1 + 2], t);
 }
 
 /* CIE 1960 uv of an XYZ colour. */
@@ -921,7 +924,7 @@ double orc_disc_temperature(double t_peak, double u) {
 /* Per-pixel render                                                          */
 /* ------------------------------------------------------------------------ */
 
-#define NDBG 20 /* channel 19: sensitivity of the pixel's Y to a one-pixel footprint shift */
+#define NDBG 23
 typedef struct {
   const orc_camera *cam;
   const orc_disc *disc;
@@ -1111,8 +1114,13 @@ static void render_pixel(render_job *J, int i, int j, pix *quad[2][2], double *o
       c_lookup(J->sc->C, J->sc->c_nx, J->sc->c_ny, J->sc->c_nd, sxyz[0] / S, sxyz[1] / S, Dst, cc);
       double s = S * d[8] * J->exposure_stars;
       for (int k = 0; k < 3; ++k) L[k] += trans * s * cc[k];
-      /* relative change of the pixel's Y per screen pixel of footprint shift */
-      d[19] = L[1] > 0.0 ? d[19] * trans * s * cc[1] / L[1] : 0.0;
+      /* bound on the change of each linear-RGB channel per screen pixel of
+       * footprint shift: |d sum/d shift| / sum (channel 19) times the star
+       * light seen through |M| (the XYZ -> RGB matrix mixes signs) */
+      for (int c = 0; c < 3; ++c)
+        d[20 + c] = d[19] * trans * s *
+                    (fabs(J->rgbm[c * 3 + 0] * cc[0]) + fabs(J->rgbm[c * 3 + 1] * cc[1]) +
+                     fabs(J->rgbm[c * 3 + 2] * cc[2]));
     }
   } else {
     d[6] = -1; d[7] = -1;
@@ -1163,7 +1171,9 @@ static void *render_worker(void *argp) {
  *  10..12 gathered star XYZ, 13 hit-0 Doppler, 14 hit-1 Doppler,
  *  15 texels visited, 16 footprint half extent (level-0 texels),
  *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|),
- *  19 |gradient| of the pixel's Y per pixel of footprint shift, relative to Y.
+ *  19 |gradient| of the star sum's Y per pixel of footprint shift, relative
+ *     to that sum, 20..22 resulting bound on the change of R, G, B per pixel
+ *     of footprint shift.
  * force_level >= 0 forces the mip level (for the flat-space checks). */
 int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc,
                double exposure_stars, const orc_scene *sc, int y0, int y1, int force_level,

@@ -3,7 +3,8 @@
 Each .cu file compiles in its own nvcc process (in parallel), then one link
 step makes ``paper_2010_08735_gb300/libbh.so``.  The cube-map builder is
 compiled without multiply-add contraction (its FP64 binning arithmetic must
-round exactly as written).
+round exactly as written); the FP32 renderer uses the approximate (2 ulp)
+division and square root.
 """
 from __future__ import annotations
 
@@ -21,8 +22,8 @@ BUILD = HERE.parent / "_build"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "--expt-relaxed-constexpr", "-I", str(HERE.parent / "include")]
-SOURCES = {"bh_core.cu": [], "bh_cubemap.cu": ["-fmad=false"], "bh_render.cu": [],
-           "bh_serve.cu": []}
+SOURCES = {"bh_core.cu": [], "bh_cubemap.cu": ["-fmad=false"],
+           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false"], "bh_serve.cu": []}
 
 
 def nvcc() -> str:

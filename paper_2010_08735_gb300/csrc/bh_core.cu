@@ -203,12 +203,66 @@ __global__ void precompute_D_kernel(int n, double *D64, T *Ds) {
   Ds[(size_t)j * n + i] = to_storage<T>(Delta);
 }
 
-// U(e,phi) per texel: x = 1/(1 + 6 e^2), y = (phi/3)(1 + 6 e^3)/(1 + e^2).
+// Warp-cooperative forms of the quadratures above: the 32 lanes of a warp
+// share the Gauss-Legendre nodes of one integral and sum them with shuffles,
+// so that the Newton iterations of one U texel run on a whole warp.
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double warp_quad_w(const Apsis &a, double w0, double w1, int panels, int lane) {
+  double h = (w1 - w0) / panels, s = 0.0;
+  for (int idx = lane; idx < panels * kGL; idx += 32) {
+    int p = idx / kGL, k = idx % kGL;
+    double c = w0 + (p + 0.5) * h, r = 0.5 * h;
+    s += cGLw[k] * r * 2.0 * rsqrt(qw(a, c + r * cGLx[k]));
+  }
+  return warp_sum(s);
+}
+
+__device__ double warp_quad_t_scatter(const Apsis &a, double c, double t0, double t1, int panels,
+                                      int lane) {
+  double h = (t1 - t0) / panels, s = 0.0;
+  for (int idx = lane; idx < panels * kGL; idx += 32) {
+    int p = idx / kGL, k = idx % kGL;
+    double m = t0 + (p + 0.5) * h, r = 0.5 * h;
+    double sh = sinh(m + r * cGLx[k]);
+    s += cGLw[k] * r * 2.0 * c * sqrt(1.0 + sh * sh) * rsqrt(qw(a, c * sh));
+  }
+  return warp_sum(s);
+}
+
+__device__ double warp_phi_scatter(const Apsis &a, double w0, int lane) {
+  double w1 = sqrt(a.ua);
+  if (a.ua > 0.6) {
+    double c = sqrt(a.A / a.B);
+    double wm = fmax(w0, fmin(w1, 0.35));
+    return warp_quad_t_scatter(a, c, asinh(w0 / c), asinh(wm / c), 6, lane) + warp_quad_w(a, wm, w1, 4, lane);
+  }
+  return warp_quad_w(a, w0, w1, 4, lane);
+}
+
+__device__ double warp_phi_plunge(double se, double ta, double tb, int lane) {
+  const int panels = 6;
+  double h = (tb - ta) / panels, s = 0.0;
+  for (int idx = lane; idx < panels * kGL; idx += 32) {
+    int p = idx / kGL, k = idx % kGL;
+    double t = ta + (p + 0.5) * h + 0.5 * h * cGLx[k];
+    double th = tanh(t);
+    s += cGLw[k] * 0.5 * h * rsqrt(1.0 + se * sinh(t) * th * th);
+  }
+  return warp_sum(s);
+}
+
+// U(e,phi) per texel, one warp per texel: x = 1/(1 + 6 e^2),
+// y = (phi/3)(1 + 6 e^3)/(1 + e^2).
 template <typename T>
 __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y;
-  if (i >= ne || j >= nphi) return;
+  int lane = threadIdx.x & 31;
+  int texel = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (texel >= ne * nphi) return;  // whole warps leave together
+  int i = texel % ne, j = texel / ne;
   double u;
   if (i == 0) {
     u = j == 0 ? 0.0 : 1.0;  // e -> infinity: radial ray, captured at once
@@ -221,11 +275,11 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
       u = 0.0;
     } else if (e2 < kMu) {
       Apsis ap = apsis_of_eta(1.0 - e2 / kMu);
-      double phia = phi_scatter(ap, 0.0);
+      double phia = warp_phi_scatter(ap, 0.0, lane);
       if (phi > phia) phi = 2.0 * phia - phi;  // past the apsis: reflection
       double lo = 0.0, hi = sqrt(ap.ua), w = 0.5 * (lo + hi);
       for (int it = 0; it < 80; ++it) {
-        double F = phi_scatter(ap, w) - phi;  // decreasing in w
+        double F = warp_phi_scatter(ap, w, lane) - phi;  // decreasing in w
         if (F > 0.0) lo = w; else hi = w;
         double dF = -2.0 * rsqrt(qw(ap, w));
         double wn = w - F / dF;
@@ -237,12 +291,12 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
     } else {
       double se = sqrt(e2 - kMu);
       double ta = asinh(-2.0 / 3.0 / se), tb = asinh(1.0 / 3.0 / se);
-      if (phi >= phi_plunge(se, ta, tb)) {
+      if (phi >= warp_phi_plunge(se, ta, tb, lane)) {
         u = 1.0;  // reached the horizon before phi (reading C7)
       } else {
         double lo = ta, hi = tb, t = 0.5 * (lo + hi);
         for (int it = 0; it < 80; ++it) {
-          double F = phi_plunge(se, ta, t) - phi;  // increasing in t
+          double F = warp_phi_plunge(se, ta, t, lane) - phi;  // increasing in t
           if (F < 0.0) lo = t; else hi = t;
           double th = tanh(t);
           double dF = rsqrt(1.0 + se * sinh(t) * th * th);
@@ -255,8 +309,10 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
       }
     }
   }
-  U64[(size_t)j * ne + i] = u;
-  Us[(size_t)j * ne + i] = to_storage<T>(u);
+  if (lane == 0) {
+    U64[(size_t)j * ne + i] = u;
+    Us[(size_t)j * ne + i] = to_storage<T>(u);
+  }
 }
 
 template <typename T>
@@ -320,13 +376,14 @@ __global__ void ctable_kernel(const double *cmf, const double *cct, float4 *C) {
       make_float4((float)(r[0] / es), (float)(r[1] / es), (float)(r[2] / es), 0.f);
 }
 
-// Disc table: ln X, ln Y, ln Z of B_T at log2 T = 8 + 12 (k + 1/2)/n.
+// Disc table: ln Y, X/Y, Z/Y of B_T at log2 T = 8 + 12 (k + 1/2)/n (one
+// exponential per lookup).
 __global__ void disc_table_kernel(const double *cmf, float4 *out) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= kDiscN) return;
   double xyz[3];
   dblackbody_xyz(cmf, exp2(8.0 + 12.0 * (k + 0.5) / kDiscN), xyz);
-  out[k] = make_float4((float)log(xyz[0]), (float)log(xyz[1]), (float)log(xyz[2]), 0.f);
+  out[k] = make_float4((float)log(xyz[1]), (float)(xyz[0] / xyz[1]), (float)(xyz[2] / xyz[1]), 0.f);
 }
 
 bh_status colour_tables_launch(bh_ctx *ctx, bh_tables *t, cudaStream_t s) {
@@ -404,6 +461,7 @@ extern "C" void bh_destroy(bh_ctx *c) {
   cudaSetDevice(c->device);
   bh::serve_destroy(c);
   cudaDeviceSynchronize();
+  c->graph.reset();
   if (c->status_dev) cudaFree(c->status_dev);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->cam_host) cudaFreeHost(c->cam_host);
@@ -468,13 +526,14 @@ extern "C" bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc
   bh_status st = tables_alloc(ctx, desc, s, &t);
   if (st) return st;
   int n = desc->d_n;
-  dim3 gd((n + 127) / 128, n), gu((desc->u_ne + 63) / 64, desc->u_nphi);
+  dim3 gd((n + 127) / 128, n);
+  unsigned gu = (unsigned)((desc->u_ne * desc->u_nphi + 3) / 4);  // 4 warps (texels) per block
   if (desc->storage == BH_F32) {
     precompute_D_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D);
-    precompute_U_kernel<float><<<gu, 64, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (float *)t->U);
+    precompute_U_kernel<float><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (float *)t->U);
   } else {
     precompute_D_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D);
-    precompute_U_kernel<__half><<<gu, 64, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (__half *)t->U);
+    precompute_U_kernel<__half><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (__half *)t->U);
   }
   count_launch(ctx, 2);
   cudaError_t e = cudaGetLastError();

@@ -153,6 +153,26 @@ __global__ void mip_kernel(const long long *psums, const uint2 *prec, int Np, in
   csums[t * 3 + 2] = sz;
 }
 
+// Occupancy bits of one level: a texel is occupied when its colour is not
+// zero.  The renderer walks only the occupied texels of a footprint row.
+__global__ void occupancy_kernel(const uint2 *rec, int NL, unsigned *mask) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int wpr = (NL + 31) / 32;
+  long long nw = 6LL * NL * wpr;
+  if (t >= nw) return;
+  long long row = t / wpr;  // face * NL + j
+  int w = (int)(t % wpr);
+  const uint2 *r = rec + row * NL;
+  unsigned bits = 0;
+  for (int b = 0; b < 32; ++b) {
+    int i = 32 * w + b;
+    if (i >= NL) break;
+    uint2 v = r[i];
+    if ((v.x | (v.y & 0xffffu)) != 0u) bits |= 1u << b;
+  }
+  mask[t] = bits;
+}
+
 }  // namespace bh
 
 using namespace bh;
@@ -189,7 +209,9 @@ extern "C" bh_status bh_build_star_cubemap(bh_ctx *ctx, const bh_star *stars, lo
   long long *sums0 = nullptr, *sums1 = nullptr;
   double *cmf = nullptr;
   bh_star *dstars = nullptr;
+  c->mask_words = mask_level_offset(N, c->levels);
   cudaError_t e = cudaMalloc((void **)&c->rec, sizeof(uint2) * c->records);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->mask, sizeof(unsigned) * c->mask_words);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&acc, sizeof(unsigned long long) * 5 * nt0, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&sums0, sizeof(long long) * 3 * nt0, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&sums1, sizeof(long long) * 3 * nt1, s);
@@ -217,6 +239,13 @@ extern "C" bh_status bh_build_star_cubemap(bh_ctx *ctx, const bh_star *stars, lo
       long long *tmp = ps;
       ps = cs;
       cs = tmp;
+    }
+    for (int L = 0; L < c->levels; ++L) {
+      int NL = N >> L;
+      long long nw = 6LL * NL * ((NL + 31) / 32);
+      occupancy_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(c->rec + cube_level_offset(N, L), NL,
+                                                                   c->mask + mask_level_offset(N, L));
+      count_launch(ctx);
     }
     e = cudaGetLastError();
   }
@@ -250,6 +279,7 @@ extern "C" void bh_cubemap_free(bh_cubemap *c) {
   cudaSetDevice(c->ctx->device);
   cudaDeviceSynchronize();
   cudaFree(c->rec);
+  cudaFree(c->mask);
   delete c;
 }
 

@@ -39,6 +39,29 @@ bh_status cuda_fail(cudaError_t e, const char *what);
 
 struct ServeState;
 
+// A batched launch as a CUDA graph: the copy of the per-camera constants
+// from pinned staging memory and the persistent render kernel.  Rebuilt when
+// the number of cameras or the kernel changes; otherwise only the kernel's
+// parameters are updated before each replay.
+struct BatchGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t copy = nullptr, kern = nullptr;
+  int n = 0, block = 0;
+  const void *func = nullptr;
+  void *cam_dev = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    copy = kern = nullptr;
+    n = block = 0;
+    func = nullptr;
+    cam_dev = nullptr;
+  }
+};
+
 struct RenderTuning {
   int warps_per_block = 8;   // block = warps * 32 threads
   int block_w = 32;          // block tile width in pixels (multiple of 8)
@@ -61,6 +84,7 @@ struct bh_ctx {
   void *tile_host = nullptr;          // pinned
   void *tile_dev = nullptr;
   int tile_cap = 0;
+  bh::BatchGraph graph;               // bh_render_batch launches
   float *frame_dev = nullptr;         // bh_render_to_host frame buffer
   size_t frame_cap = 0;
   bh::RenderTuning tuning;
@@ -74,7 +98,7 @@ struct bh_tables {
   double *D64 = nullptr, *U64 = nullptr;  // FP64 values
   void *D = nullptr, *U = nullptr;        // storage copies read by the renderer
   float4 *C = nullptr;                    // colour shift table [k][j][i] (XYZ, pad)
-  float4 *disc = nullptr;                 // ln XYZ of black bodies, log2 T in [8, 20]
+  float4 *disc = nullptr;                 // ln Y, X/Y, Z/Y of black bodies, log2 T in [8, 20]
 };
 
 struct bh_cubemap {
@@ -84,12 +108,24 @@ struct bh_cubemap {
   bh_dtype storage = BH_F16;
   uint2 *rec = nullptr;  // all levels
   long long records = 0;
+  unsigned *mask = nullptr;  // occupancy bits: one per texel, rows padded to 32-bit words
+  long long mask_words = 0;
 };
 
 namespace bh {
 inline long long cube_level_offset(int N, int L) {
   long long off = 0;
   for (int l = 0; l < L; ++l) off += 6LL * (N >> l) * (N >> l);
+  return off;
+}
+// Occupancy mask layout: level-major, face, row; a row of n texels takes
+// (n + 31) / 32 words, bit (i & 31) of word i / 32 is texel i.
+inline long long mask_level_offset(int N, int L) {
+  long long off = 0;
+  for (int l = 0; l < L; ++l) {
+    long long n = N >> l;
+    off += 6LL * n * ((n + 31) / 32);
+  }
   return off;
 }
 inline int cube_levels(int N) {

@@ -23,10 +23,11 @@ constexpr int kMaxLevels = 14;
 // Per-camera constants, computed on the host in FP64 (Eq. staticbasis,
 // Eq. camerabasis, the boost B(v) of Appendix C, Eq. d) and rounded to float.
 struct CamConst {
-  float A[9];       // row r (static e_r, e_theta, e_phi), column c (camera e_w, e_h, e_d): spatial parts
-  float b[3];       // spatial part of -e_tau
+  float Ot[9];      // O^T: camera (e_w, e_h, e_d) components -> boosted (r', theta', phi') components
+  float w[3];       // unit velocity direction on the camera axes (0 if v = 0)
+  float vhat[3];    // unit velocity direction on (e_r, e_theta, e_phi) (0 if v = 0)
+  float beta, inv_gamma2;
   float R[9];       // static orthonormal -> pseudo-Cartesian: columns sqrt(1-u) r^, theta^, phi^
-  float v[3];       // camera velocity on (e_r, e_theta, e_phi)
   float x[3];       // e_x' = position direction r^
   float zdeg[3];    // e_z' for radial beams (reading C8)
   float gamma, f, u, inv_sqrt_1mu;
@@ -49,8 +50,10 @@ struct RenderParams {
   const float4 *C;
   const float4 *disc;
   const uint2 *cube;
+  const unsigned *cube_mask;  // occupancy bits, one per texel
   int cube_n, cube_levels, cube_bf16;
   long long level_off[kMaxLevels];
+  long long mask_off[kMaxLevels];
   float u_ic, u_oc, t_peak, rho;
   float fmax_disc;          // max of u^3 (1 - sqrt(3u)), at u = 12/49
   int disc_on;
@@ -93,8 +96,17 @@ __device__ __forceinline__ float d_x(float e2, float em) {
   return 0.5f + sqrtf(fmaxf(-lg, 0.f) * 0.02f);
 }
 
+#ifndef BH_RENDER_MIN_BLOCKS
+#define BH_RENDER_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget must allow
+#endif
+
+// Exact float value of a byte (0..255) without an int-to-float conversion.
+__device__ __forceinline__ float byte_to_float(unsigned b) {
+  return __uint_as_float(0x4B000000u | b) - 8388608.f;
+}
+
 template <typename DT, bool DEBUG>
-__global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
+__global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const RenderParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
   float4 *s_disc = reinterpret_cast<float4 *>(smem);
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
     f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
     int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
     float t = f - k0;
-    y_peak = expf(fmaf(t, s_disc[k1].y - s_disc[k0].y, s_disc[k0].y));
+    y_peak = expf(fmaf(t, s_disc[k1].x - s_disc[k0].x, s_disc[k0].x));
   }
 
   for (int tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
@@ -170,14 +182,29 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
     int px = tx * P.bw + wx * 8 + lx, py = ty * P.bh + wy * 4 + ly;
 
     // ---- beam initialisation (Eq. d, Eq. raybasis, Eq. alpha)
-    float qw = (px + 0.5f) - C.half_w, qh = C.half_h - (py + 0.5f);
-    float inv = rsqrtf(fmaf(qw, qw, fmaf(qh, qh, C.f * C.f)));
-    float q0 = qw * inv, q1 = qh * inv, q2 = -C.f * inv;
-    float ds0 = fmaf(C.A[0], q0, fmaf(C.A[1], q1, fmaf(C.A[2], q2, C.b[0])));
-    float ds1 = fmaf(C.A[3], q0, fmaf(C.A[4], q1, fmaf(C.A[5], q2, C.b[1])));
-    float ds2 = fmaf(C.A[6], q0, fmaf(C.A[7], q1, fmaf(C.A[8], q2, C.b[2])));
+    float qw = (px + 0.5f) - C.half_w, qh = C.half_h - (py + 0.5f), qd = -C.f;
+    float qq = fmaf(qw, qw, fmaf(qh, qh, qd * qd));
+    float inv = rsqrtf(qq), nq = qq * inv;
+    float q0 = qw * inv, q1 = qh * inv, q2 = qd * inv;
+    // Aberration (Eq. d): the backward direction -e_tau + n, on the static
+    // frame, keeps n's part across v and has gamma (n.v^ - beta) along v^.
+    // n.v^ - beta = (|q|^2/gamma^2 - |q x w|^2) / (|q| (q.w + beta |q|)) for
+    // forward beams, free of the cancellation of n.v^ - beta near 1 - beta.
+    float wq = fmaf(C.w[0], qw, fmaf(C.w[1], qh, C.w[2] * qd));
+    float dpar;
+    if (wq > 0.f) {
+      float x0_ = qh * C.w[2] - qd * C.w[1], x1_ = qd * C.w[0] - qw * C.w[2], x2_ = qw * C.w[1] - qh * C.w[0];
+      float c2 = fmaf(x0_, x0_, fmaf(x1_, x1_, x2_ * x2_));
+      dpar = C.gamma * (fmaf(qq, C.inv_gamma2, -c2) / (nq * fmaf(C.beta, nq, wq)));
+    } else {
+      dpar = C.gamma * fmaf(wq, inv, -C.beta);
+    }
+    float p0 = (qw - wq * C.w[0]) * inv, p1 = (qh - wq * C.w[1]) * inv, p2 = (qd - wq * C.w[2]) * inv;
+    float ds0 = fmaf(C.Ot[0], p0, fmaf(C.Ot[1], p1, fmaf(C.Ot[2], p2, dpar * C.vhat[0])));
+    float ds1 = fmaf(C.Ot[3], p0, fmaf(C.Ot[4], p1, fmaf(C.Ot[5], p2, dpar * C.vhat[1])));
+    float ds2 = fmaf(C.Ot[6], p0, fmaf(C.Ot[7], p1, fmaf(C.Ot[8], p2, dpar * C.vhat[2])));
     float dsn = sqrtf(fmaf(ds0, ds0, fmaf(ds1, ds1, ds2 * ds2)));
-    float dcam = C.gamma * (1.f + fmaf(C.v[0], ds0, fmaf(C.v[1], ds1, C.v[2] * ds2)) / dsn);
+    float dcam = C.gamma * fmaf(C.beta, dpar / dsn, 1.f);
     float d0 = fmaf(C.R[0], ds0, fmaf(C.R[1], ds1, C.R[2] * ds2));
     float d1 = fmaf(C.R[3], ds0, fmaf(C.R[4], ds1, C.R[5] * ds2));
     float d2 = fmaf(C.R[6], ds0, fmaf(C.R[7], ds1, C.R[8] * ds2));
@@ -310,10 +337,10 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
           int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
           float tt = f - k0;
           float4 a = s_disc[k0], b = s_disc[k1];
-          float w = trans * sc;
-          LX = fmaf(w, expf(fmaf(tt, b.x - a.x, a.x)), LX);
-          LY = fmaf(w, expf(fmaf(tt, b.y - a.y, a.y)), LY);
-          LZ = fmaf(w, expf(fmaf(tt, b.z - a.z, a.z)), LZ);
+          float wy = trans * sc * expf(fmaf(tt, b.x - a.x, a.x));  // (ln Y, X/Y, Z/Y) table
+          LX = fmaf(wy, fmaf(tt, b.y - a.y, a.y), LX);
+          LY += wy;
+          LZ = fmaf(wy, fmaf(tt, b.z - a.z, a.z), LZ);
         }
         trans *= 1.f - P.rho;
       }
@@ -388,16 +415,34 @@ __global__ void __launch_bounds__(256) render_kernel(const RenderParams P) {
           int j0 = max((int)floorf(cT - htL), 0), j1 = min((int)floorf(cT + htL), NL - 1);
           const uint2 *rec = P.cube + P.level_off[L] + (long long)face * NL * NL;
           float lscale = (float)(1 << (2 * L));
+          // star at (ii + (ps + 1/2)/256, jj + (pt + 1/2)/256) in level-L texels
+          const float q11 = i11 * (1.f / 256.f), q12 = i12 * (1.f / 256.f);
+          const float q21 = i21 * (1.f / 256.f), q22 = i22 * (1.f / 256.f);
+          // One footprint row at a time: the row's occupancy bits select the
+          // texels that hold stars; only those records are read.
+          const int nrow = i1 - i0 + 1;
+          const float ds0 = (i0 - cS) + 0.5f / 256.f;
+          const int wpr = (NL + 31) >> 5;
+          const unsigned *mrows = P.cube_mask + P.mask_off[L] + (long long)face * NL * wpr;
+          const int w0i = i0 >> 5, b0 = i0 & 31;
+          const unsigned rowbits = nrow >= 32 ? 0xffffffffu : (1u << nrow) - 1u;
           for (int jj = j0; jj <= j1; ++jj) {
-            float dt = (jj - cT);
-            for (int ii = i0; ii <= i1; ++ii) {
-              ++visited;
-              uint2 r = __ldg(rec + (long long)jj * NL + ii);
-              if ((r.x | (r.y & 0xffffu)) == 0u) continue;  // empty texel: X = Y = Z = +0
+            const float dt = (jj - cT) + 0.5f / 256.f;
+            const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
+            const uint2 *rowp = rec + (long long)jj * NL + i0;
+            const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
+            unsigned long long win = __ldg(mrow);
+            if (b0 + nrow > 32 && w0i + 1 < wpr) win |= (unsigned long long)__ldg(mrow + 1) << 32;
+            unsigned bits = (unsigned)(win >> b0) & rowbits;
+            visited += nrow;
+            while (bits) {
+              const int k = __ffs(bits) - 1;
+              bits &= bits - 1u;
+              const uint2 r = __ldg(rowp + k);
               unsigned pw = r.y >> 16;
-              float ds_ = (ii - cS) + ((pw & 255u) + 0.5f) * (1.f / 256.f);
-              float dt_ = dt + ((pw >> 8) + 0.5f) * (1.f / 256.f);
-              float w = fmaf(i11, ds_, i12 * dt_), h = fmaf(i21, ds_, i22 * dt_);
+              float ps = byte_to_float(pw & 255u), pt = byte_to_float(pw >> 8);
+              float w = fmaf(q11, ps, fmaf(q12, pt, fmaf(i11, (float)k, wrow)));
+              float h = fmaf(q21, ps, fmaf(q22, pt, fmaf(i21, (float)k, hrow)));
               float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
               if (fw <= 0.f || fh <= 0.f) continue;
               float X, Y, Z;
@@ -519,30 +564,27 @@ static void camera_constants(const bh_camera *c, CamConst *k) {
   const double *v = c->v;
   double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   double g = 1.0 / sqrt(1.0 - v2);
-  // boosted spatial axes e'_j, static components (t; r, theta, phi)
-  double Bt[3], Bs[3][3];
+  // The boost B(v) keeps the components across v and scales the one along v
+  // (the camera's 4-velocity is gamma (1, v) on the static frame); the
+  // camera axes e_w, e_h, e_d are O e' (rows of O on the boosted axes).
+  double vn = sqrt(v2);
+  double vh[3] = {0.0, 0.0, 0.0};
+  if (vn > 0.0)
+    for (int j = 0; j < 3; ++j) vh[j] = v[j] / vn;
   for (int j = 0; j < 3; ++j) {
-    Bt[j] = g * v[j];
-    for (int m = 0; m < 3; ++m) Bs[j][m] = (j == m ? 1.0 : 0.0) + (v2 > 0.0 ? (g - 1.0) * v[j] * v[m] / v2 : 0.0);
+    for (int col = 0; col < 3; ++col) k->Ot[j * 3 + col] = (float)c->orient[col * 3 + j];
+    double wc = 0.0;
+    for (int m = 0; m < 3; ++m) wc += c->orient[j * 3 + m] * vh[m];
+    k->w[j] = (float)wc;
+    k->vhat[j] = (float)vh[j];
   }
-  (void)Bt;
-  // camera axes e_w, e_h, e_d = O e'
-  double Es[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int m = 0; m < 3; ++m) {
-      double s = 0.0;
-      for (int j = 0; j < 3; ++j) s += c->orient[i * 3 + j] * Bs[j][m];
-      Es[i][m] = s;
-    }
-  for (int r = 0; r < 3; ++r)
-    for (int col = 0; col < 3; ++col) k->A[r * 3 + col] = (float)Es[col][r];
-  for (int r = 0; r < 3; ++r) k->b[r] = (float)(-g * v[r]);
+  k->beta = (float)vn;
+  k->inv_gamma2 = (float)(1.0 - v2);
   double s1 = sqrt(1.0 - u);
   for (int r = 0; r < 3; ++r) {
     k->R[r * 3 + 0] = (float)(s1 * rh[r]);
     k->R[r * 3 + 1] = (float)th[r];
     k->R[r * 3 + 2] = (float)ph[r];
-    k->v[r] = (float)v[r];
     k->x[r] = (float)rh[r];
   }
   // radial beams (reading C8): e_z' = x ^ (least-aligned axis) / |.|
@@ -612,7 +654,11 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
     P.cube_n = cube->n;
     P.cube_levels = cube->levels;
     P.cube_bf16 = cube->storage == BH_BF16;
-    for (int L = 0; L < cube->levels && L < kMaxLevels; ++L) P.level_off[L] = cube_level_offset(cube->n, L);
+    P.cube_mask = cube->mask;
+    for (int L = 0; L < cube->levels && L < kMaxLevels; ++L) {
+      P.level_off[L] = cube_level_offset(cube->n, L);
+      P.mask_off[L] = mask_level_offset(cube->n, L);
+    }
   }
   P.disc_on = disc->enabled ? 1 : 0;
   P.u_ic = disc->enabled ? (float)(1.0 / disc->r_in) : 0.f;
@@ -670,6 +716,7 @@ static bh_status render_one(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
 
 static bh_status ensure_cam_staging(bh_ctx *ctx, int n) {
   if (n <= ctx->cam_cap) return BH_OK;
+  ctx->graph.reset();
   if (ctx->cam_host) cudaFreeHost(ctx->cam_host);
   if (ctx->cam_dev) cudaFree(ctx->cam_dev);
   ctx->cam_host = ctx->cam_dev = nullptr;
@@ -681,9 +728,15 @@ static bh_status ensure_cam_staging(bh_ctx *ctx, int n) {
   return BH_OK;
 }
 
+static const void *kernel_ptr(bool half, bool debug) {
+  if (!half) return debug ? (const void *)render_kernel<float, true> : (const void *)render_kernel<float, false>;
+  return debug ? (const void *)render_kernel<__half, true> : (const void *)render_kernel<__half, false>;
+}
+
 bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
                             const bh_camera *cams, const bh_disc *disc, const bh_shading *sh,
-                            float *const *outs, cudaStream_t s, void *cam_host, void *cam_dev) {
+                            float *const *outs, cudaStream_t s, void *cam_host, void *cam_dev,
+                            BatchGraph *bg) {
   RenderParams P;
   fill_params(ctx, t, cube, disc, sh, P);
   CamConst *h = static_cast<CamConst *>(cam_host);
@@ -696,11 +749,38 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
     h[k].dbg = nullptr;
     tiles += h[k].tiles_x * ((cams[k].height + P.bh - 1) / P.bh);
   }
-  BH_CUDA(cudaMemcpyAsync(cam_dev, h, sizeof(CamConst) * n, cudaMemcpyHostToDevice, s));
   P.cams = static_cast<const CamConst *>(cam_dev);
   P.ncams = n;
   P.total_tiles = tiles;
-  return launch(ctx, t, P, false, s);
+  int threads = 32 * ctx->tuning.warps_per_block;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
+  int grid = std::min(P.total_tiles, ctx->sm_count * ctx->tuning.blocks_per_sm);
+  if (grid < 1) return BH_OK;
+  const void *func = kernel_ptr(t->desc.storage == BH_F16, false);
+  void *args[] = {&P};
+  cudaKernelNodeParams kp = {};
+  kp.func = const_cast<void *>(func);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  if (!bg->exec || bg->n != n || bg->func != func || bg->cam_dev != cam_dev || bg->block != threads) {
+    bg->reset();
+    BH_CUDA(cudaGraphCreate(&bg->graph, 0));
+    BH_CUDA(cudaGraphAddMemcpyNode1D(&bg->copy, bg->graph, nullptr, 0, cam_dev, cam_host,
+                                     sizeof(CamConst) * n, cudaMemcpyHostToDevice));
+    BH_CUDA(cudaGraphAddKernelNode(&bg->kern, bg->graph, &bg->copy, 1, &kp));
+    BH_CUDA(cudaGraphInstantiate(&bg->exec, bg->graph, 0));
+    bg->n = n;
+    bg->block = threads;
+    bg->func = func;
+    bg->cam_dev = cam_dev;
+  } else {
+    BH_CUDA(cudaGraphExecKernelNodeSetParams(bg->exec, bg->kern, &kp));
+  }
+  BH_CUDA(cudaGraphLaunch(bg->exec, s));
+  count_launch(ctx);
+  return BH_OK;
 }
 
 size_t cam_const_size() { return sizeof(CamConst); }
@@ -772,7 +852,8 @@ extern "C" bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *t, const bh_c
   BH_CUDA(cudaStreamSynchronize(s));
   st = ensure_cam_staging(ctx, n);
   if (st) return st;
-  return render_batch_impl(ctx, t, cube, n, cams, disc, sh, outs, s, ctx->cam_host, ctx->cam_dev);
+  return render_batch_impl(ctx, t, cube, n, cams, disc, sh, outs, s, ctx->cam_host, ctx->cam_dev,
+                           &ctx->graph);
 }
 
 extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
@@ -801,7 +882,8 @@ extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh
     float tot = 0.f;
     for (int rep = 0; rep < 4 && st == BH_OK; ++rep) {
       cudaEventRecord(e0, s);
-      st = render_batch_impl(ctx, t, cube, n, cams, disc, sh, outs, s, ctx->cam_host, ctx->cam_dev);
+      st = render_batch_impl(ctx, t, cube, n, cams, disc, sh, outs, s, ctx->cam_host, ctx->cam_dev,
+                             &ctx->graph);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0.f;

@@ -23,7 +23,8 @@ namespace bh {
 
 bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
                             const bh_camera *cams, const bh_disc *disc, const bh_shading *sh,
-                            float *const *outs, cudaStream_t s, void *cam_host, void *cam_dev);
+                            float *const *outs, cudaStream_t s, void *cam_host, void *cam_dev,
+                            BatchGraph *bg);
 bh_status validate_batch(int n, const bh_camera *cams, const bh_disc *disc, float *const *outs);
 size_t cam_const_size();
 void serve_destroy(bh_ctx *ctx);
@@ -47,6 +48,7 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   void *cam_host = nullptr, *cam_dev = nullptr;
+  BatchGraph graph;
   std::vector<Request> batch;
   bool busy = false;
 };
@@ -89,6 +91,7 @@ void serve_destroy(bh_ctx *ctx) {
   if (!S) return;
   for (auto &sl : S->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
+    sl.graph.reset();
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.cam_host) cudaFreeHost(sl.cam_host);
@@ -134,7 +137,7 @@ static bh_status progress(bh_ctx *ctx) {
     }
     bh_status st = render_batch_impl(ctx, first.tables, first.cube, (int)sl.batch.size(), S->cams.data(),
                                      &first.disc, &first.sh, S->outs.data(), sl.stream, sl.cam_host,
-                                     sl.cam_dev);
+                                     sl.cam_dev, &sl.graph);
     if (st) return st;
     BH_CUDA(cudaEventRecord(sl.done, sl.stream));
     sl.busy = true;

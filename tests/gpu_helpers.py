@@ -67,31 +67,43 @@ def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndar
     near_dn = has & (lvl > 0) & (prev < 1 + level_margin)
     near_face = has & (dbg[..., 17] < face_margin)
     degenerate = has & (dbg[..., 18] < 1e-5)
-    return m | near_up | near_dn | near_face | degenerate | star_ill_conditioned(dbg)
+    return m | near_up | near_dn | near_face | degenerate
 
 
-# FP32 places a beam's escape direction to about one float ulp of the angle
-# (2.4e-7 rad near 2), i.e. up to about 1e-3 of a 4K pixel; a pixel whose value
-# changes by more than 1 % for a 1e-3 px shift of its footprint (a bright star
-# near the edge of its tent filter) is ill-conditioned for a per-pixel
-# relative comparison.  The oracle reports that sensitivity (|gradient of the
-# star sum| / star sum, per pixel of shift, scaled by the star share of the
-# pixel).
-POS_EPS_PX = 1e-3
-KAPPA_MAX = 0.01 / POS_EPS_PX
+# FP32 places a beam's escape direction to a few float ulps of the angle,
+# about 1e-6 rad.  In screen pixels of footprint shift that is
+# 1e-6 * sqrt(Omega/Omega') / (pixel angle): about 1e-3 px for a 4K pixel,
+# far less for a coarse image.  A pixel whose linear RGB can change by more
+# than 1 % for that shift (a bright star near the edge of its tent filter,
+# amplified where the XYZ -> RGB matrix cancels) is ill-conditioned for a
+# per-pixel relative comparison.  The oracle reports, per channel, a bound on
+# the change per pixel of shift (channels 20..22) and Omega/Omega' (8).
+POS_EPS_RAD = 1e-6
 
 
-def star_ill_conditioned(dbg: np.ndarray) -> np.ndarray:
-    return dbg[..., 19] > KAPPA_MAX
+def pos_eps_px(dbg: np.ndarray, cam: dict) -> np.ndarray:
+    pix = cam["fov_y"] / cam["height"]
+    return POS_EPS_RAD * np.sqrt(np.maximum(dbg[..., 8], 0.0)) / pix
 
 
-def ill_conditioned_ok(rel: np.ndarray, dbg: np.ndarray, mask_other: np.ndarray) -> bool:
+def rgb_sensitivity(dbg: np.ndarray, orc: np.ndarray) -> np.ndarray:
+    o = orc[..., :3]
+    floor = 1e-4 * max(np.abs(o).max(), 1e-30)
+    return (dbg[..., 20:23] / np.maximum(np.abs(o), floor)).max(axis=-1)
+
+
+def star_ill_conditioned(dbg: np.ndarray, orc: np.ndarray, cam: dict) -> np.ndarray:
+    return rgb_sensitivity(dbg, orc) * pos_eps_px(dbg, cam) > RGB_MAX_REL
+
+
+def ill_conditioned_ok(rel: np.ndarray, dbg: np.ndarray, orc: np.ndarray, cam: dict,
+                       mask_other: np.ndarray) -> bool:
     """Validity of the pixels masked only for conditioning: their error stays
-    within what a 3e-3 px footprint shift explains, plus the base tolerance."""
-    sel = star_ill_conditioned(dbg) & ~mask_other
+    within what three times that shift explains, plus the base tolerance."""
+    sel = star_ill_conditioned(dbg, orc, cam) & ~mask_other
     if not sel.any():
         return True
-    bound = RGB_MAX_REL + 3 * POS_EPS_PX * dbg[..., 19][sel]
+    bound = RGB_MAX_REL + 3 * (pos_eps_px(dbg, cam) * rgb_sensitivity(dbg, orc))[sel]
     return bool(np.all(rel[sel] <= bound))
 
 

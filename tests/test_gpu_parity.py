@@ -212,12 +212,12 @@ def check_stages(gd, od, mask):
         assert (gd[..., 7][has] != od[..., 7][has]).mean() < 1e-3
 
 
-def check_rgb(og, oo, od, mask):
-    mean, mx, rel = image_error(og, oo, mask)
+def check_rgb(og, oo, od, mask, cam):
+    ill = star_ill_conditioned(od, oo, cam)
+    mean, mx, rel = image_error(og, oo, mask | ill)
     assert mean <= RGB_MEAN_REL and mx <= RGB_MAX_REL, (mean, mx)
-    other = mask & ~star_ill_conditioned(od)
-    assert star_ill_conditioned(od).mean() < 0.10
-    assert ill_conditioned_ok(rel, od, other)
+    assert ill.mean() < 0.10
+    assert ill_conditioned_ok(rel, od, oo, cam, mask)
 
 
 def test_render_static_256(ctx, orc, gpu_tables, static_scene):
@@ -227,7 +227,7 @@ def test_render_static_256(ctx, orc, gpu_tables, static_scene):
                                           name="static_256")
     assert mask.mean() < 0.2
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask)
+    check_rgb(og, oo, od, mask, wk["camera"])
 
 
 def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_scene):
@@ -236,7 +236,7 @@ def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_sce
     og, gd, oo, od, mask = compare_render(orc, ctx, uploaded_tables, cube, scene, wk["camera"],
                                           wk["disc"], name="static_256_uploaded")
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask)
+    check_rgb(og, oo, od, mask, wk["camera"])
 
 
 @pytest.mark.parametrize("cam", [
@@ -253,7 +253,7 @@ def test_render_configs_small(ctx, orc, gpu_tables, static_scene, cam):
     og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, cam, disc,
                                           name=f"small_{cam['width']}x{cam['height']}_r{cam['r']}")
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask)
+    check_rgb(og, oo, od, mask, cam)
 
 
 def test_star_centroids_sparse_field(ctx, orc, orc_tables, orc_colour, gpu_tables):
@@ -381,4 +381,4 @@ def test_full_size_sampled_rows(ctx, orc, orc_tables, orc_colour, gpu_tables, na
     finally:
         bh.bh_cubemap_free(cube)
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask)
+    check_rgb(og, oo, od, mask, wk["camera"])
