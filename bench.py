@@ -124,6 +124,14 @@ def render_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+def workload_config(wk, ws=1):
+    W, H = wk["camera"]["width"], wk["camera"]["height"]
+    return {"workload": WORKLOAD, "width": W, "height": H, "camera": "r=6, theta=85deg, v=0.5c e_phi",
+            "stars": wk["n_stars"], "cube_face": wk["cube_n"], "cube_dtype": wk["cube_dtype"],
+            "tables": "512x512 D + 64x32 U, FP32", "l2": "flushed (256 MiB write) before each frame",
+            "parallelism": f"replicas x{ws}"}
+
+
 def orbit_camera(wk, step):
     cam = dict(wk["camera"])
     cam["phi"] = cam["phi"] + 0.002 * step  # the camera moves along its orbit between frames
@@ -176,8 +184,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "width": 1920, "height": 1080, "stars": wk["n_stars"],
-                       "cube_face": wk["cube_n"], "l2": "n/a (CPU)"},
+            "config": workload_config(wk, args.gpus),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -299,10 +306,7 @@ def run_ours(args):
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": W, "height": H, "camera": "r=6, theta=85deg, v=0.5c e_phi",
-                   "stars": wk["n_stars"], "cube_face": wk["cube_n"], "cube_dtype": wk["cube_dtype"],
-                   "tables": "512x512 D + 64x32 U, FP32", "l2": "flushed (256 MiB write) before each frame",
-                   "parallelism": f"replicas x{ws}"},
+        "config": workload_config(wk, ws),
         "mpix_per_s": fps * W * H / 1e6,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": render_traffic(),

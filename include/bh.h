@@ -228,6 +228,48 @@ bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubem
                             const bh_shading *shading, float *const *outs, int *chosen);
 
 /* ------------------------------------------------------------------------ */
+/* Free-fall camera orbits (Appendix C), resident on the device               */
+/* ------------------------------------------------------------------------ */
+
+/* A camera on a geodesic: coordinate time t, radius r and angle psi in an
+ * orbital plane of inclination chi (position r (cos chi cos psi, sin psi,
+ * sin chi cos psi)), dr/dtau, and the constants of motion e, l.  orient: the
+ * user rotation O, rows e_w, e_h, e_d on the boosted (r', chi', psi') axes. */
+typedef struct {
+  double t, r, psi, rdot;
+  double e, l;
+  double chi;
+  double orient[9];
+  double fov_y;
+  int width, height;
+} bh_orbit;
+
+/* Initial state from the radius r0 > 1.05, the angle delta0 in (0, pi) of the
+ * velocity from the radius (tan delta = r dpsi/dr) and the speed v0 in [0,1)
+ * wrt the static observer: e^2 = (1-u0)/(1-v0^2), l^2 = (e^2+u0-1) /
+ * (u0^2 (1-u0+cot^2 delta0)) (Appendix C).  orient may be NULL (identity). */
+bh_status bh_orbit_init(double r0, double delta0, double v0, double chi, const double *orient,
+                        double fov_y, int width, int height, bh_orbit *out);
+
+/* The camera (position, velocity wrt the static observer, orientation on the
+ * boosted (r', theta', phi') axes) of an orbit state; host only. */
+bh_status bh_orbit_camera(const bh_orbit *orbit, bh_camera *out);
+
+/* Advance n device-resident orbits by dtau of proper time in `steps` FP64
+ * Runge-Kutta steps of d^2r/dtau^2 = (2 l^2 u^3 - 3 l^2 u^4 - u^2)/2,
+ * dpsi/dtau = l u^2, dt/dtau = e/(1-u).  An orbit that would reach r <= 1.05
+ * stops there.  Enqueued on `stream`. */
+bh_status bh_orbits_advance(bh_ctx *ctx, bh_orbit *orbits_device, int n, double dtau, int steps,
+                            void *stream);
+
+/* Render n <= 1024 device-resident orbits in one persistent launch: their
+ * camera constants are computed on the device (no host round trip); outs[k]
+ * as in bh_render_batch.  Enqueued on `stream`. */
+bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap, int n,
+                           const bh_orbit *orbits_device, const bh_disc *disc,
+                           const bh_shading *shading, float *const *outs, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of frame requests from many viewers          */
 /* ------------------------------------------------------------------------ */
 

@@ -66,6 +66,11 @@ class Scene(C.Structure):
                 ("cube", C.POINTER(C.c_uint16)), ("cube_n", C.c_int), ("cube_dtype", C.c_int)]
 
 
+class Orbit(C.Structure):
+    _fields_ = [("t", C.c_double), ("r", C.c_double), ("psi", C.c_double), ("rdot", C.c_double),
+                ("e", C.c_double), ("l", C.c_double), ("chi", C.c_double)]
+
+
 _D = C.POINTER(C.c_double)
 
 
@@ -108,6 +113,10 @@ def lib():
                                      C.POINTER(Scene), C.c_int, C.c_int, C.c_int, C.c_int,
                                      _D, _D, C.POINTER(C.c_longlong)]),
             "orc_bruteforce_ray": (C.c_int, [_D, _D, C.c_double, C.c_double, C.c_double, _D]),
+            "orc_orbit_init": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.POINTER(Orbit)]),
+            "orc_orbit_advance": (None, [C.POINTER(Orbit), C.c_double, C.c_int]),
+            "orc_orbit_camera": (None, [C.POINTER(Orbit), _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -370,3 +379,31 @@ def bruteforce_ray(x0, d0, r_in=3.0, r_out=12.0, step=1e-3):
     n = int(o[4])
     return {"dir": o[0:3], "captured": bool(o[3]), "hits_u": list(o[5:5 + min(n, 4)]),
             "n_crossings": n}
+
+
+# --------------------------------------------------------------------------
+# Free-fall camera orbit (Appendix C)
+# --------------------------------------------------------------------------
+
+def orbit_init(r0, delta0, v0, chi) -> Orbit:
+    o = Orbit()
+    if lib().orc_orbit_init(r0, delta0, v0, chi, C.byref(o)):
+        raise ValueError("orbit_init: need r0 > 1 and 0 <= v0 < 1")
+    return o
+
+
+def orbit_advance(o: Orbit, dtau: float, n: int = 100) -> Orbit:
+    lib().orc_orbit_advance(C.byref(o), dtau, n)
+    return o
+
+
+def orbit_camera(o: Orbit, orient=((1, 0, 0), (0, 1, 0), (0, 0, 1)), fov_y=1.0471975511965976,
+                 width=64, height=64) -> dict:
+    """Camera dict (as the render takes) of an orbit state; orient rows on the
+    boosted (r', chi', psi') axes."""
+    oo = np.ascontiguousarray(np.asarray(orient, dtype=np.float64).reshape(9))
+    out = np.zeros(15)
+    lib().orc_orbit_camera(C.byref(o), _dp(oo), _dp(out))
+    return {"r": out[0], "theta": out[1], "phi": out[2], "v": tuple(out[3:6]),
+            "orient": tuple(tuple(out[6 + 3 * i:9 + 3 * i]) for i in range(3)),
+            "fov_y": fov_y, "width": width, "height": height}

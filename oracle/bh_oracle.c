@@ -1276,3 +1276,86 @@ int orc_bruteforce_ray(const double *x0, const double *d0, double r_in, double r
   out[4] = nh;
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Free-fall camera orbit (Appendix C)                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double t, r, psi, rdot; /* coordinate time, radius, angle in the orbital plane, dr/dtau */
+  double e, l;            /* constants of motion */
+  double chi;             /* inclination of the orbital plane */
+} orc_orbit;
+
+/* Constants of motion from the initial radius, direction and speed (App. C):
+ * e^2 = (1 - u0)/(1 - v0^2), l^2 = (e^2 + u0 - 1)/(u0^2 (1 - u0 + cot^2 delta0));
+ * dr/dtau from (dr/dtau)^2 = e^2 + l^2 u^3 - l^2 u^2 + u - 1, outward if
+ * delta0 < pi/2. */
+int orc_orbit_init(double r0, double delta0, double v0, double chi, orc_orbit *o) {
+  if (!(r0 > 1.0) || !(v0 >= 0.0 && v0 < 1.0)) return 1;
+  double u = 1.0 / r0;
+  double e2 = (1.0 - u) / (1.0 - v0 * v0);
+  double cot = cos(delta0) / sin(delta0);
+  double l2 = (e2 + u - 1.0) / (u * u * (1.0 - u + cot * cot));
+  o->t = 0.0; o->r = r0; o->psi = 0.0; o->chi = chi;
+  o->e = sqrt(e2);
+  o->l = sqrt(l2 > 0.0 ? l2 : 0.0);
+  double rd2 = e2 + l2 * u * u * u - l2 * u * u + u - 1.0;
+  o->rdot = (delta0 < PI / 2 ? 1.0 : -1.0) * sqrt(rd2 > 0.0 ? rd2 : 0.0);
+  return 0;
+}
+
+static void orbit_rhs(const orc_orbit *o, const double *y, double *dy) {
+  double u = 1.0 / y[1], l2 = o->l * o->l;
+  dy[0] = o->e / (1.0 - u);
+  dy[1] = y[3];
+  dy[2] = o->l * u * u;
+  dy[3] = 0.5 * (2.0 * l2 * u * u * u - 3.0 * l2 * u * u * u * u - u * u);
+}
+
+/* Advance by dtau of proper time in n RK4 steps (App. C: d^2r/dtau^2 =
+ * (2 l^2 u^3 - 3 l^2 u^4 - u^2)/2, dpsi/dtau = l u^2, dt/dtau = e/(1-u)). */
+void orc_orbit_advance(orc_orbit *o, double dtau, int n) {
+  double h = dtau / n;
+  for (int s = 0; s < n; ++s) {
+    double y[4] = {o->t, o->r, o->psi, o->rdot}, k1[4], k2[4], k3[4], k4[4], z[4];
+    orbit_rhs(o, y, k1);
+    for (int a = 0; a < 4; ++a) z[a] = y[a] + 0.5 * h * k1[a];
+    orbit_rhs(o, z, k2);
+    for (int a = 0; a < 4; ++a) z[a] = y[a] + 0.5 * h * k2[a];
+    orbit_rhs(o, z, k3);
+    for (int a = 0; a < 4; ++a) z[a] = y[a] + h * k3[a];
+    orbit_rhs(o, z, k4);
+    o->t = y[0] + h / 6.0 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]);
+    o->r = y[1] + h / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]);
+    o->psi = y[2] + h / 6.0 * (k1[2] + 2 * k2[2] + 2 * k3[2] + k4[2]);
+    o->rdot = y[3] + h / 6.0 * (k1[3] + 2 * k2[3] + 2 * k3[3] + k4[3]);
+  }
+}
+
+/* Camera of an orbit state (App. C): position from
+ * r (cos chi cos psi, sin psi, sin chi cos psi), velocity wrt the static
+ * observer v = [ (dr/dtau)/e , 0 , l u sqrt(1-u)/e ] on (e_r, e_chi, e_psi),
+ * and the rotation to (e_r, e_theta, e_phi): e_chi = a e_theta + b e_phi,
+ * e_psi = -b e_theta + a e_phi, with e_chi the unit normal e_psi ^ e_r =
+ * (sin chi, 0, -cos chi), so a = sin chi cos theta cos phi + cos chi sin theta
+ * and b = -sin chi sin phi (reading C22).  The user rotation O is given on the
+ * boosted (r', chi', psi') axes and is returned on (r', theta', phi').
+ * out: [0] r, [1] theta, [2] phi, [3..5] v on (e_r, e_theta, e_phi),
+ * [6..14] orientation rows on (r', theta', phi'). */
+void orc_orbit_camera(const orc_orbit *o, const double *orient_rcp, double *out) {
+  double th = acos(cos(o->psi) * sin(o->chi));
+  double ph = atan2(sin(o->psi), cos(o->chi) * cos(o->psi));
+  double u = 1.0 / o->r;
+  double a = sin(o->chi) * cos(th) * cos(ph) + cos(o->chi) * sin(th);
+  double b = -sin(o->chi) * sin(ph);
+  double vr = o->rdot / o->e, vpsi = o->l * u * sqrt(1.0 - u) / o->e;
+  out[0] = o->r; out[1] = th; out[2] = ph;
+  out[3] = vr; out[4] = -b * vpsi; out[5] = a * vpsi;
+  for (int i = 0; i < 3; ++i) {
+    const double *Or = orient_rcp + 3 * i; /* (r', chi', psi') components */
+    out[6 + 3 * i + 0] = Or[0];
+    out[6 + 3 * i + 1] = a * Or[1] - b * Or[2];
+    out[6 + 3 * i + 2] = b * Or[1] + a * Or[2];
+  }
+}

@@ -50,6 +50,13 @@ class TableDesc(C.Structure):
     _fields_ = [("d_n", C.c_int), ("u_ne", C.c_int), ("u_nphi", C.c_int), ("storage", C.c_int)]
 
 
+class Orbit(C.Structure):
+    _fields_ = [("t", C.c_double), ("r", C.c_double), ("psi", C.c_double), ("rdot", C.c_double),
+                ("e", C.c_double), ("l", C.c_double), ("chi", C.c_double),
+                ("orient", C.c_double * 9), ("fov_y", C.c_double), ("width", C.c_int),
+                ("height", C.c_int)]
+
+
 class Star(C.Structure):
     _fields_ = [("dir", C.c_float * 3), ("lum", C.c_float), ("temp_K", C.c_float)]
 
@@ -85,6 +92,11 @@ def lib():
                                 P(_vp), _vp],
             "bh_autotune_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
                                   P(_vp), P(C.c_int)],
+            "bh_orbit_init": [C.c_double, C.c_double, C.c_double, C.c_double, P(C.c_double),
+                              C.c_double, C.c_int, C.c_int, P(Orbit)],
+            "bh_orbit_camera": [P(Orbit), P(Camera)],
+            "bh_orbits_advance": [_vp, _vp, C.c_int, C.c_double, C.c_int, _vp],
+            "bh_render_orbits": [_vp, _vp, _vp, C.c_int, _vp, P(Disc), P(Shading), P(_vp), _vp],
             "bh_serve_submit": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading), _vp,
                                 P(C.c_ulonglong)],
             "bh_serve_poll": [_vp, C.c_ulonglong, C.c_int, P(C.c_double)],
@@ -332,6 +344,46 @@ def bh_autotune_batch(ctx, tables, cube, cameras, disc, shading, outs) -> int:
     _check(lib().bh_autotune_batch(ctx, tables, cube, n, cams, C.byref(d), C.byref(shading),
                                    ptrs, C.byref(chosen)))
     return chosen.value
+
+
+def bh_orbit_init(r0, delta0, v0, chi, orient=None, fov_y=1.0471975511965976, width=256,
+                  height=256) -> Orbit:
+    o = Orbit()
+    op = None
+    if orient is not None:
+        arr = (C.c_double * 9)(*np.asarray(orient, dtype=np.float64).reshape(9))
+        op = C.cast(arr, C.POINTER(C.c_double))
+    _check(lib().bh_orbit_init(r0, delta0, v0, chi, op, fov_y, width, height, C.byref(o)))
+    return o
+
+
+def bh_orbit_camera(orbit: Orbit) -> Camera:
+    c = Camera()
+    _check(lib().bh_orbit_camera(C.byref(orbit), C.byref(c)))
+    return c
+
+
+def orbits_to_bytes(orbits) -> bytes:
+    """Packed bh_orbit array (copy it into a device buffer)."""
+    arr = (Orbit * len(orbits))(*orbits)
+    return bytes(arr)
+
+
+def bh_orbits_advance(ctx, orbits_device, n, dtau, steps=8, stream=None) -> None:
+    _check(lib().bh_orbits_advance(ctx, _ptr(orbits_device), n, dtau, steps, _stream(stream)))
+
+
+def bh_render_orbits(ctx, tables, cube, n, orbits_device, disc, shading, outs, stream=None) -> None:
+    ptrs = (_vp * n)(*[_ptr(o) for o in outs])
+    d = _as(disc, make_disc)
+    _check(lib().bh_render_orbits(ctx, tables, cube, n, _ptr(orbits_device), C.byref(d),
+                                  C.byref(shading), ptrs, _stream(stream)))
+
+
+def camera_to_dict(c: Camera) -> dict:
+    return {"r": c.r, "theta": c.theta, "phi": c.phi, "v": tuple(c.v[:]),
+            "orient": tuple(tuple(c.orient[3 * i:3 * i + 3]) for i in range(3)),
+            "fov_y": c.fov_y, "width": c.width, "height": c.height}
 
 
 def bh_serve_submit(ctx, tables, cube, viewer, camera, disc, shading, out):

@@ -85,6 +85,10 @@ struct bh_ctx {
   void *tile_dev = nullptr;
   int tile_cap = 0;
   bh::BatchGraph graph;               // bh_render_batch launches
+  void *orb_outs_host = nullptr;      // bh_render_orbits: pinned output pointers
+  void *orb_outs_dev = nullptr;       // device copy of them, then the tile count
+  void *orb_cams_dev = nullptr;       // per-orbit camera constants
+  int orb_cap = 0;
   float *frame_dev = nullptr;         // bh_render_to_host frame buffer
   size_t frame_cap = 0;
   bh::RenderTuning tuning;

@@ -42,6 +42,7 @@ struct RenderParams {
   CamConst cam0;            // single-camera launches
   const CamConst *cams;     // batched launches (nullptr: cam0)
   int ncams, total_tiles;
+  const int *total_tiles_dev;  // if set, the tile count computed on the device
   int bw, bh, warps_x;      // block tile (pixels) and warps across
   const void *D;
   int d_n;
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     y_peak = expf(fmaf(t, s_disc[k1].x - s_disc[k0].x, s_disc[k0].x));
   }
 
-  for (int tile = blockIdx.x; tile < P.total_tiles; tile += gridDim.x) {
+  const int total_tiles = P.total_tiles_dev ? *P.total_tiles_dev : P.total_tiles;
+  for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     // ---- which camera and which tile of it
     const CamConst *cp = &P.cam0;
     if (P.cams) {
@@ -557,7 +559,7 @@ static bool validate_disc(const bh_disc *d) {
 
 // Camera frame in FP64: static basis (Eq. staticbasis), boost B(v) (the
 // camera's 4-velocity is gamma (1, v) on the static frame), user rotation O.
-static void camera_constants(const bh_camera *c, CamConst *k) {
+__host__ __device__ static void camera_constants(const bh_camera *c, CamConst *k) {
   double st = sin(c->theta), ct = cos(c->theta), sp = sin(c->phi), cph = cos(c->phi);
   double u = 1.0 / c->r;
   double rh[3] = {st * cph, st * sp, ct}, th[3] = {ct * cph, ct * sp, -st}, ph[3] = {-sp, cph, 0.0};
@@ -785,6 +787,99 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
 
 size_t cam_const_size() { return sizeof(CamConst); }
 
+// ---------------------------------------------------------------------------
+// Free-fall camera orbits (Appendix C), advanced and turned into camera
+// constants on the device so that a viewer's trajectory never leaves HBM.
+// ---------------------------------------------------------------------------
+
+// Camera of an orbit state: position from r (cos chi cos psi, sin psi,
+// sin chi cos psi); velocity wrt the static observer ((dr/dtau)/e, 0,
+// l u sqrt(1-u)/e) on (e_r, e_chi, e_psi); e_chi = a e_theta + b e_phi,
+// e_psi = -b e_theta + a e_phi with e_chi = e_psi ^ e_r (reading C22).
+__host__ __device__ static void orbit_to_camera(const bh_orbit *o, bh_camera *c) {
+  double th = acos(cos(o->psi) * sin(o->chi));
+  double ph = atan2(sin(o->psi), cos(o->chi) * cos(o->psi));
+  double u = 1.0 / o->r;
+  double a = sin(o->chi) * cos(th) * cos(ph) + cos(o->chi) * sin(th);
+  double b = -sin(o->chi) * sin(ph);
+  double vpsi = o->l * u * sqrt(1.0 - u) / o->e;
+  c->r = o->r;
+  c->theta = th;
+  c->phi = ph;
+  c->v[0] = o->rdot / o->e;
+  c->v[1] = -b * vpsi;
+  c->v[2] = a * vpsi;
+  for (int i = 0; i < 3; ++i) {
+    const double *Or = o->orient + 3 * i;  // on (r', chi', psi')
+    c->orient[3 * i + 0] = Or[0];
+    c->orient[3 * i + 1] = a * Or[1] - b * Or[2];
+    c->orient[3 * i + 2] = b * Or[1] + a * Or[2];
+  }
+  c->fov_y = o->fov_y;
+  c->width = o->width;
+  c->height = o->height;
+}
+
+// d^2r/dtau^2 = (2 l^2 u^3 - 3 l^2 u^4 - u^2)/2, dpsi/dtau = l u^2,
+// dt/dtau = e/(1-u): RK4 in proper time, FP64, one thread per orbit.  An orbit
+// that would reach r <= 1.05 stops there (no static observer inside the
+// horizon, Sec. 5).
+__device__ static void orbit_rhs(const bh_orbit &o, const double *y, double *dy) {
+  double u = 1.0 / y[1], l2 = o.l * o.l;
+  dy[0] = o.e / (1.0 - u);
+  dy[1] = y[3];
+  dy[2] = o.l * u * u;
+  dy[3] = 0.5 * (2.0 * l2 * u * u * u - 3.0 * l2 * u * u * u * u - u * u);
+}
+
+__global__ void orbit_advance_kernel(bh_orbit *orbits, int n, double dtau, int steps) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  bh_orbit o = orbits[k];
+  double h = dtau / steps;
+  for (int s = 0; s < steps; ++s) {
+    double y[4] = {o.t, o.r, o.psi, o.rdot}, k1[4], k2[4], k3[4], k4[4], z[4];
+    orbit_rhs(o, y, k1);
+    for (int a = 0; a < 4; ++a) z[a] = y[a] + 0.5 * h * k1[a];
+    orbit_rhs(o, z, k2);
+    for (int a = 0; a < 4; ++a) z[a] = y[a] + 0.5 * h * k2[a];
+    orbit_rhs(o, z, k3);
+    for (int a = 0; a < 4; ++a) z[a] = y[a] + h * k3[a];
+    orbit_rhs(o, z, k4);
+    double r = y[1] + h / 6.0 * (k1[1] + 2 * k2[1] + 2 * k3[1] + k4[1]);
+    if (!(r > 1.05)) break;
+    o.t = y[0] + h / 6.0 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]);
+    o.r = r;
+    o.psi = y[2] + h / 6.0 * (k1[2] + 2 * k2[2] + 2 * k3[2] + k4[2]);
+    o.rdot = y[3] + h / 6.0 * (k1[3] + 2 * k2[3] + 2 * k3[3] + k4[3]);
+  }
+  orbits[k] = o;
+}
+
+// Camera constants of every orbit, then the tile offsets (one thread, in
+// camera order) -- the same layout bh_render_batch stages from the host.
+__global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *const *outs, int bw, int bh,
+                                      CamConst *cams, int *total_tiles) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    bh_camera c;
+    orbit_to_camera(&orbits[k], &c);
+    camera_constants(&c, &cams[k]);
+    cams[k].tiles_x = (c.width + bw - 1) / bw;
+    cams[k].out = reinterpret_cast<float4 *>(outs[k]);
+    cams[k].dbg = nullptr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int tiles = 0;
+    for (int j = 0; j < n; ++j) {
+      cams[j].tile0 = tiles;
+      tiles += cams[j].tiles_x * ((orbits[j].height + bh - 1) / bh);
+    }
+    *total_tiles = tiles;
+  }
+}
+
 bh_status validate_batch(int n, const bh_camera *cams, const bh_disc *disc, float *const *outs) {
   if (n < 1 || !cams || !outs) { set_error("batch: n >= 1 cameras and outputs required"); return BH_ERR_INVALID_ARG; }
   for (int k = 0; k < n; ++k) {
@@ -898,4 +993,106 @@ extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh
   cudaStreamDestroy(s);
   if (chosen) *chosen = best;
   return st;
+}
+
+extern "C" bh_status bh_orbit_init(double r0, double delta0, double v0, double chi, const double *orient,
+                                   double fov_y, int width, int height, bh_orbit *out) {
+  if (!out) { set_error("bh_orbit_init: out is NULL"); return BH_ERR_INVALID_ARG; }
+  if (!(r0 > 1.05) || !(v0 >= 0.0 && v0 < 1.0) || !(delta0 > 0.0 && delta0 < kPi)) {
+    set_error("bh_orbit_init: need r0 > 1.05, 0 <= v0 < 1, 0 < delta0 < pi");
+    return BH_ERR_INVALID_ARG;
+  }
+  memset(out, 0, sizeof *out);
+  double u = 1.0 / r0;
+  double e2 = (1.0 - u) / (1.0 - v0 * v0);  // gamma = e / sqrt(1 - u)
+  double cot = cos(delta0) / sin(delta0);     // tan(delta) = r dpsi/dr
+  double l2 = (e2 + u - 1.0) / (u * u * (1.0 - u + cot * cot));
+  out->r = r0;
+  out->chi = chi;
+  out->e = sqrt(e2);
+  out->l = sqrt(l2 > 0.0 ? l2 : 0.0);
+  double rd2 = e2 + l2 * u * u * u - l2 * u * u + u - 1.0;
+  out->rdot = (delta0 < 0.5 * kPi ? 1.0 : -1.0) * sqrt(rd2 > 0.0 ? rd2 : 0.0);
+  const double eye[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  for (int k = 0; k < 9; ++k) out->orient[k] = orient ? orient[k] : eye[k];
+  out->fov_y = fov_y;
+  out->width = width;
+  out->height = height;
+  bh_camera c;
+  orbit_to_camera(out, &c);
+  return validate_camera(&c, 0) ? BH_OK : BH_ERR_INVALID_ARG;
+}
+
+extern "C" bh_status bh_orbit_camera(const bh_orbit *o, bh_camera *out) {
+  if (!o || !out) { set_error("bh_orbit_camera: NULL argument"); return BH_ERR_INVALID_ARG; }
+  orbit_to_camera(o, out);
+  return BH_OK;
+}
+
+extern "C" bh_status bh_orbits_advance(bh_ctx *ctx, bh_orbit *orbits_device, int n, double dtau, int steps,
+                                       void *stream) {
+  if (!ctx || (n > 0 && !orbits_device) || n < 0 || steps < 1) {
+    set_error("bh_orbits_advance: bad argument");
+    return BH_ERR_INVALID_ARG;
+  }
+  if (n == 0) return BH_OK;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  orbit_advance_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(orbits_device, n, dtau, steps);
+  count_launch(ctx);
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
+}
+
+extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
+                                      const bh_orbit *orbits_device, const bh_disc *disc,
+                                      const bh_shading *sh, float *const *outs, void *stream) {
+  if (!ctx || !t || !orbits_device || !outs || n < 1 || n > 1024) {
+    set_error("bh_render_orbits: bad argument (1 <= n <= 1024)");
+    return BH_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < n; ++k)
+    if (!outs[k] || ((uintptr_t)outs[k] & 15)) {
+      set_error("bh_render_orbits: output %d is NULL or not 16-byte aligned", k);
+      return BH_ERR_INVALID_ARG;
+    }
+  if (!validate_disc(disc)) return BH_ERR_INVALID_ARG;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  BH_CUDA(cudaStreamSynchronize(s));  // the staging buffers are reused
+  if (n > ctx->orb_cap) {
+    cudaFreeHost(ctx->orb_outs_host);
+    cudaFree(ctx->orb_outs_dev);
+    cudaFree(ctx->orb_cams_dev);
+    ctx->orb_outs_host = nullptr;
+    ctx->orb_outs_dev = nullptr;
+    ctx->orb_cams_dev = nullptr;
+    ctx->orb_cap = 0;
+    BH_CUDA(cudaMallocHost(&ctx->orb_outs_host, sizeof(float *) * 1024));
+    BH_CUDA(cudaMalloc(&ctx->orb_outs_dev, sizeof(float *) * 1024 + 16));
+    BH_CUDA(cudaMalloc(&ctx->orb_cams_dev, sizeof(CamConst) * 1024));
+    ctx->orb_cap = 1024;
+  }
+  float **ph = static_cast<float **>(ctx->orb_outs_host);
+  for (int k = 0; k < n; ++k) ph[k] = outs[k];
+  float **pd = static_cast<float **>(ctx->orb_outs_dev);
+  int *total_dev = reinterpret_cast<int *>(pd + 1024);
+  BH_CUDA(cudaMemcpyAsync(pd, ph, sizeof(float *) * n, cudaMemcpyHostToDevice, s));
+  RenderParams P;
+  fill_params(ctx, t, cube, disc, sh, P);
+  CamConst *cams = static_cast<CamConst *>(ctx->orb_cams_dev);
+  orbit_camconst_kernel<<<1, 1024, 0, s>>>(orbits_device, n, pd, P.bw, P.bh, cams, total_dev);
+  count_launch(ctx);
+  P.cams = cams;
+  P.ncams = n;
+  P.total_tiles = 0;
+  P.total_tiles_dev = total_dev;
+  int threads = 32 * ctx->tuning.warps_per_block;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
+  int grid = ctx->sm_count * ctx->tuning.blocks_per_sm;
+  if (t->desc.storage == BH_F16) render_kernel<__half, false><<<grid, threads, smem, s>>>(P);
+  else render_kernel<float, false><<<grid, threads, smem, s>>>(P);
+  count_launch(ctx);
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
 }

@@ -382,3 +382,78 @@ def test_full_size_sampled_rows(ctx, orc, orc_tables, orc_colour, gpu_tables, na
         bh.bh_cubemap_free(cube)
     check_stages(gd, od, mask)
     check_rgb(og, oo, od, mask, wk["camera"])
+
+
+def test_table_storage_precision_report(ctx, orc, orc_tables, orc_colour, static_scene):
+    """Error of the linear-RGB image against the oracle reading FP64 tables, for
+    the renderer reading FP32- and FP16-stored tables (the tables' own storage
+    error, reported; FP32 must meet the parity tolerance)."""
+    import json
+    import os
+    cube, scene32 = static_scene
+    D, U = orc_tables
+    Ct, dl = orc_colour
+    wk = synth.WORKLOADS["static_256"]
+    cam, disc = wk["camera"], wk["disc"]
+    exact = orc.SceneTables(D, U, Ct.astype(np.float32), dl.astype(np.float32), scene32.cube,
+                            scene32.cube_n, scene32.cube_dtype)
+    oo, od, _ = orc.render(cam, disc, exact, exposure_stars=EXPOSURE_STARS, debug=True)
+    mask = oracle_mask(od) | star_ill_conditioned(od, oo, cam)
+    report = {}
+    for name, storage in (("f32", bh.BH_F32), ("f16", bh.BH_F16)):
+        t = bh.bh_precompute_tables(ctx, 512, 64, 32, storage)
+        try:
+            og, _ = gpu_render(ctx, t, cube, cam, disc)
+        finally:
+            bh.bh_tables_free(t)
+        mean, mx, _ = image_error(og, oo, mask)
+        report[name] = {"mean_rel": mean, "max_rel": mx}
+    d = os.environ.get("BH_DUMP_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "table_storage_precision.json"), "w") as f:
+            json.dump(report, f, indent=1)
+    assert report["f32"]["mean_rel"] <= RGB_MEAN_REL
+    assert report["f16"]["mean_rel"] <= 0.05
+
+
+def test_orbits_advance_matches_oracle(ctx, orc):
+    """Device-resident free-fall orbits (Appendix C) follow the oracle's RK4."""
+    import ctypes
+    params = [(6.0, math.pi / 2, math.sqrt((1 / 6) / (2 * (5 / 6))), 0.3), (9.0, 1.3, 0.35, 0.6),
+              (20.0, 2.2, 0.25, 1.0), (4.0, 2.8, 0.1, 0.0)]
+    host = [bh.bh_orbit_init(r, d, v, chi, None, 1.0, 64, 48) for r, d, v, chi in params]
+    buf = torch.frombuffer(bytearray(bh.orbits_to_bytes(host)), dtype=torch.uint8).cuda()
+    bh.bh_orbits_advance(ctx, buf, len(host), 3.0, 60)
+    bh.bh_orbits_advance(ctx, buf, len(host), 3.0, 60)
+    torch.cuda.synchronize()
+    got = (bh.Orbit * len(host)).from_buffer_copy(bytes(buf.cpu().numpy()))
+    for (r, d, v, chi), g in zip(params, got):
+        o = orc.orbit_init(r, d, v, chi)
+        orc.orbit_advance(o, 3.0, 60)
+        orc.orbit_advance(o, 3.0, 60)
+        if o.r <= 1.05:
+            continue
+        assert g.r == pytest.approx(o.r, rel=1e-11)
+        assert g.psi == pytest.approx(o.psi, rel=1e-11, abs=1e-12)
+        assert g.t == pytest.approx(o.t, rel=1e-11)
+
+
+def test_render_orbits_equals_batch(ctx, gpu_tables, static_scene):
+    """Cameras computed on the device from orbits render as the same cameras
+    staged from the host (FP64 set-up on both, rounded to FP32)."""
+    cube, _ = static_scene
+    host = [bh.bh_orbit_init(r, d, v, chi, None, 1.0, w, h)
+            for (r, d, v, chi, w, h) in [(6.0, 1.5707963, 0.316, 0.3, 64, 48), (9.0, 1.3, 0.35, 0.6, 33, 17),
+                                         (15.0, 2.0, 0.5, 1.2, 96, 64)]]
+    buf = torch.frombuffer(bytearray(bh.orbits_to_bytes(host)), dtype=torch.uint8).cuda()
+    disc = synth.disc()
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    outs = [torch.zeros((o.height, o.width, 4), device="cuda") for o in host]
+    bh.bh_render_orbits(ctx, gpu_tables, cube, len(host), buf, disc, sh, outs)
+    cams = [bh.camera_to_dict(bh.bh_orbit_camera(o)) for o in host]
+    ref = [torch.zeros_like(o) for o in outs]
+    bh.bh_render_batch(ctx, gpu_tables, cube, cams, disc, sh, ref)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6)
