@@ -70,6 +70,19 @@ const char *bh_last_error(void);
  * points), for launch accounting. */
 long long bh_kernel_launches(const bh_ctx *ctx);
 
+/* Synchronise `stream` and read the context's kernel status word: BH_OK, or
+ * BH_ERR_TIMEOUT if a render's bounded wait for its shared-memory tables gave
+ * up (the block skipped its tiles), or BH_ERR_DEVICE_STATUS.  Clears the word. */
+bh_status bh_check_status(bh_ctx *ctx, void *stream);
+
+/* Failure detection tests: make the next render launch of this context, after
+ * its tables have landed, also wait on a barrier that nothing arrives at (kind
+ * BH_FAULT_TABLE_WAIT), so that its bounded wait (2 ms) runs out, the blocks
+ * skip their tiles and bh_check_status reports BH_ERR_TIMEOUT; the context
+ * stays usable.  No fault, trap or hang is produced. */
+#define BH_FAULT_TABLE_WAIT 1
+bh_status bh_inject_fault(bh_ctx *ctx, int kind);
+
 /* ------------------------------------------------------------------------ */
 /* Tables D(e,u), U(e,phi) (Algorithm 1 PRECOMPUTE, Sec. 3.3.2-3.3.3,        */
 /* Appendix A) and the colour tables (Sec. 3.4.2)                             */

@@ -101,6 +101,8 @@ def lib():
                                 P(C.c_ulonglong)],
             "bh_serve_poll": [_vp, C.c_ulonglong, C.c_int, P(C.c_double)],
             "bh_serve_flush": [_vp],
+            "bh_check_status": [_vp, _vp],
+            "bh_inject_fault": [_vp, C.c_int],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -202,6 +204,18 @@ def bh_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
 
 def bh_destroy(ctx: int) -> None:
     lib().bh_destroy(ctx)
+
+
+BH_FAULT_TABLE_WAIT = 1
+
+
+def bh_check_status(ctx: int, stream=None) -> int:
+    """BH_OK, or raises BhError (BH_ERR_TIMEOUT / BH_ERR_DEVICE_STATUS)."""
+    return _check(lib().bh_check_status(ctx, _stream(stream)))
+
+
+def bh_inject_fault(ctx: int, kind: int = BH_FAULT_TABLE_WAIT) -> None:
+    _check(lib().bh_inject_fault(ctx, kind))
 
 
 def bh_kernel_launches(ctx: int) -> int:

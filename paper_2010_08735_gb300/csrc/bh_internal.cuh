@@ -93,6 +93,7 @@ struct bh_ctx {
   size_t frame_cap = 0;
   bh::RenderTuning tuning;
   bh::ServeState *serve = nullptr;
+  int inject_table_wait = 0;          // bh_inject_fault: next render's table wait never completes
   std::mutex mu;
 };
 

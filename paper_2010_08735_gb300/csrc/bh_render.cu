@@ -61,6 +61,9 @@ struct RenderParams {
   float exp_disc, exp_stars;
   float M[9];               // XYZ -> linear sRGB
   unsigned *status;
+  unsigned long long wait_ns;  // bound of the table-load wait
+  int inject_wait;          // fault injection: also wait on a barrier nothing arrives at
+  unsigned long long inject_wait_ns;
 };
 
 __device__ __forceinline__ float ld_tab(const float *p, int i) { return __ldg(p + i); }
@@ -110,14 +113,17 @@ template <typename DT, bool DEBUG>
 __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const RenderParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
+  __shared__ __align__(8) unsigned long long mbar_never;  // fault injection: nothing arrives
   float4 *s_disc = reinterpret_cast<float4 *>(smem);
   const DT *s_U = reinterpret_cast<const DT *>(smem + sizeof(float4) * kDiscN);
 
   // ---- stage U and the disc table into shared memory with the bulk-copy engine
   unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+  unsigned mb_never = (unsigned)__cvta_generic_to_shared(&mbar_never);
   if (threadIdx.x == 0) {
     unsigned bytes = (unsigned)(sizeof(float4) * kDiscN + P.u_bytes);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_never));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
     unsigned dst0 = (unsigned)__cvta_generic_to_shared(s_disc);
@@ -133,16 +139,27 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
   }
   __syncthreads();
   {
-    unsigned done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-      asm volatile(
-          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-          : "=r"(done)
-          : "r"(mb)
-          : "memory");
-    }
-    // every thread of the block sees the same barrier; a timeout means the copy never landed
-    if (!done) {
+    // bounded waits: give up after a limit of global time
+    auto bounded_wait = [](unsigned bar, unsigned long long limit_ns) -> bool {
+      unsigned done = 0;
+      unsigned long long t0, t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      for (;;) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+        if (done) return true;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) return false;
+      }
+    };
+    bool ok = bounded_wait(mb, P.wait_ns);
+    if (!ok) bounded_wait(mb, P.wait_ns);  // let copies still in flight land before leaving
+    // fault injection (bh_inject_fault): a barrier nothing arrives at
+    if (ok && P.inject_wait) ok = bounded_wait(mb_never, P.inject_wait_ns);
+    if (!ok) {
       if (threadIdx.x == 0) atomicOr(P.status, kStatusMbarTimeout);
       return;
     }
@@ -321,28 +338,33 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float LX = 0.f, LY = 0.f, LZ = 0.f, trans = 1.f;
     float dop0 = 0.f, dop1 = 0.f;
     if (nh > 0) {
-      float e = sqrtf(e2);
-      float sc = P.rho * P.exp_disc / y_peak;
+      // nu/nu' for an emitter on the circular orbit at u' (Eq. Doppler, Eq. k_prime):
+      // gamma (1 + beta.d^) / (gamma' (1 + beta'.d^')) sqrt((1-u')/(1-u)) simplifies to
+      // dcam sqrt(2 - 3u') / (sqrt(1-u) (sqrt(2) + u'^(3/2) (e_z.e_z') / e)).
+      const float ie = rsqrtf(e2);
+      const float dpre = dcam * C.inv_sqrt_1mu;
+      const float sc = P.rho * P.exp_disc / y_peak;
+      const float lg_tpeak = log2f(P.t_peak), lg_fmax = log2f(P.fmax_disc);
       for (int h = 0; h < nh; ++h) {
         float up = h == 0 ? hu0 : hu1;
-        float fu = up * up * up * (1.f - sqrtf(3.f * up));
-        float T = fu > 0.f ? P.t_peak * sqrtf(sqrtf(fu / P.fmax_disc)) : 0.f;
-        float bp = sqrtf(up / (2.f * (1.f - up)));
-        float gp = rsqrtf(1.f - bp * bp);
-        float bd = bp * (up * sqrtf(1.f - up) / e) * z2;
-        float Dk = dcam / (gp * (1.f + bd)) * sqrtf(1.f - up) * C.inv_sqrt_1mu;
+        float su = sqrtf(up);
+        float Dk = dpre * sqrtf(2.f - 3.f * up) / fmaf(up * su * z2, ie, 1.41421356f);
         if (h == 0) dop0 = Dk; else dop1 = Dk;
-        float TT = Dk * T;
-        if (TT >= 256.f) {
-          float f = (log2f(TT) - 8.f) / 12.f * kDiscN - 0.5f;
-          f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
-          int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
-          float tt = f - k0;
-          float4 a = s_disc[k0], b = s_disc[k1];
-          float wy = trans * sc * expf(fmaf(tt, b.x - a.x, a.x));  // (ln Y, X/Y, Z/Y) table
-          LX = fmaf(wy, fmaf(tt, b.y - a.y, a.y), LX);
-          LY += wy;
-          LZ = fmaf(wy, fmaf(tt, b.z - a.z, a.z), LZ);
+        // T^4 ~ u^3 (1 - sqrt(3u)), T = t_peak at the maximum: log2(D T)
+        float fu = up * up * up * (1.f - 1.7320508f * su);
+        if (fu > 0.f) {
+          float lgT = log2f(Dk) + lg_tpeak + 0.25f * (log2f(fu) - lg_fmax);
+          if (lgT >= 8.f) {  // D T >= 256 K
+            float f = (lgT - 8.f) * (kDiscN / 12.f) - 0.5f;
+            f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
+            int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
+            float tt = f - k0;
+            float4 a = s_disc[k0], b = s_disc[k1];
+            float wy = trans * sc * expf(fmaf(tt, b.x - a.x, a.x));  // (ln Y, X/Y, Z/Y) table
+            LX = fmaf(wy, fmaf(tt, b.y - a.y, a.y), LX);
+            LY += wy;
+            LZ = fmaf(wy, fmaf(tt, b.z - a.z, a.z), LZ);
+          }
         }
         trans *= 1.f - P.rho;
       }
@@ -427,40 +449,78 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           const int wpr = (NL + 31) >> 5;
           const unsigned *mrows = P.cube_mask + P.mask_off[L] + (long long)face * NL * wpr;
           const int w0i = i0 >> 5, b0 = i0 & 31;
-          const unsigned rowbits = nrow >= 32 ? 0xffffffffu : (1u << nrow) - 1u;
-          for (int jj = j0; jj <= j1; ++jj) {
+          const unsigned rowbits = nrow <= 0 ? 0u : nrow >= 32 ? 0xffffffffu : (1u << nrow) - 1u;
+          // The star at texel (jj, ii) of this level (accumulated into S*).
+          auto take = [&](const int jj, const int k) {
             const float dt = (jj - cT) + 0.5f / 256.f;
             const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
             const uint2 *rowp = rec + (long long)jj * NL + i0;
-            const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
-            unsigned long long win = __ldg(mrow);
-            if (b0 + nrow > 32 && w0i + 1 < wpr) win |= (unsigned long long)__ldg(mrow + 1) << 32;
-            unsigned bits = (unsigned)(win >> b0) & rowbits;
-            visited += nrow;
-            while (bits) {
-              const int k = __ffs(bits) - 1;
-              bits &= bits - 1u;
-              const uint2 r = __ldg(rowp + k);
-              unsigned pw = r.y >> 16;
-              float ps = byte_to_float(pw & 255u), pt = byte_to_float(pw >> 8);
-              float w = fmaf(q11, ps, fmaf(q12, pt, fmaf(i11, (float)k, wrow)));
-              float h = fmaf(q21, ps, fmaf(q22, pt, fmaf(i21, (float)k, hrow)));
-              float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
-              if (fw <= 0.f || fh <= 0.f) continue;
-              float X, Y, Z;
-              if (P.cube_bf16) {
-                X = __uint_as_float(r.x << 16);
-                Y = __uint_as_float(r.x & 0xffff0000u);
-                Z = __uint_as_float(r.y << 16);
-              } else {
-                X = __half2float(__ushort_as_half((unsigned short)(r.x & 0xffffu)));
-                Y = __half2float(__ushort_as_half((unsigned short)(r.x >> 16)));
-                Z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
+            const uint2 r = __ldg(rowp + k);
+            unsigned pw = r.y >> 16;
+            float ps = byte_to_float(pw & 255u), pt = byte_to_float(pw >> 8);
+            float w = fmaf(q11, ps, fmaf(q12, pt, fmaf(i11, (float)k, wrow)));
+            float h = fmaf(q21, ps, fmaf(q22, pt, fmaf(i21, (float)k, hrow)));
+            float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
+            if (fw <= 0.f || fh <= 0.f) return;
+            float X, Y, Z;
+            if (P.cube_bf16) {
+              X = __uint_as_float(r.x << 16);
+              Y = __uint_as_float(r.x & 0xffff0000u);
+              Z = __uint_as_float(r.y << 16);
+            } else {
+              X = __half2float(__ushort_as_half((unsigned short)(r.x & 0xffffu)));
+              Y = __half2float(__ushort_as_half((unsigned short)(r.x >> 16)));
+              Z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
+            }
+            float wt = fw * fh * lscale;
+            SX = fmaf(wt, X, SX);
+            SY = fmaf(wt, Y, SY);
+            SZ = fmaf(wt, Z, SZ);
+          };
+          const int nrows = j1 - j0 + 1;
+          const bool straddle = b0 + nrow > 32 && w0i + 1 < wpr;
+          if (nrows > 0 && nrow > 0) visited += nrows * nrow;
+          if (nrows <= 10 && nrow <= 10) {
+            // all rows' occupancy bits first (independent loads), packed as
+            // bit 10 r + k for row j0 + r, column i0 + k; then the set bits
+            unsigned long long lo = 0ull, hi = 0ull;
+#pragma unroll
+            for (int rr = 0; rr < 10; ++rr) {
+              if (rr < nrows) {
+                const unsigned *mrow = mrows + (long long)(j0 + rr) * wpr + w0i;
+                unsigned long long win = __ldg(mrow);
+                if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
+                const unsigned long long bits = (win >> b0) & rowbits;
+                const int off = 10 * rr;
+                if (off < 64) {
+                  lo |= bits << off;
+                  if (off + 10 > 64) hi |= bits >> (64 - off);
+                } else {
+                  hi |= bits << (off - 64);
+                }
               }
-              float wt = fw * fh * lscale;
-              SX = fmaf(wt, X, SX);
-              SY = fmaf(wt, Y, SY);
-              SZ = fmaf(wt, Z, SZ);
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              unsigned long long m = half ? hi : lo;
+              while (m) {
+                const int idx = __ffsll((long long)m) - 1 + 64 * half;
+                m &= m - 1ull;
+                const int rr = idx / 10;
+                take(j0 + rr, idx - 10 * rr);
+              }
+            }
+          } else {
+            for (int jj = j0; jj <= j1; ++jj) {  // rounding at the level edge
+              const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
+              unsigned long long win = __ldg(mrow);
+              if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
+              unsigned bits = (unsigned)(win >> b0) & rowbits;
+              while (bits) {
+                const int k = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                take(jj, k);
+              }
             }
           }
         }
@@ -672,6 +732,13 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
   P.exp_stars = sh ? sh->exposure_stars : 0.01f;
   xyz_to_srgb(P.M);
   P.status = ctx->status_dev;
+  P.wait_ns = 200000000ull;  // 0.2 s: the copies take microseconds
+  P.inject_wait = 0;
+  P.inject_wait_ns = 2000000ull;  // 2 ms
+  if (ctx->inject_table_wait) {
+    P.inject_wait = 1;
+    ctx->inject_table_wait = 0;
+  }
   P.bw = ctx->tuning.block_w;
   P.warps_x = P.bw / 8;
   P.bh = 4 * (ctx->tuning.warps_per_block / P.warps_x);
@@ -856,12 +923,12 @@ __global__ void orbit_advance_kernel(bh_orbit *orbits, int n, double dtau, int s
   orbits[k] = o;
 }
 
-// Camera constants of every orbit, then the tile offsets (one thread, in
-// camera order) -- the same layout bh_render_batch stages from the host.
+// Camera constants of every orbit (one block), then the tile offsets (one
+// thread, in camera order) -- the same layout bh_render_batch stages from the
+// host.
 __global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *const *outs, int bw, int bh,
                                       CamConst *cams, int *total_tiles) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
     bh_camera c;
     orbit_to_camera(&orbits[k], &c);
     camera_constants(&c, &cams[k]);
@@ -1081,7 +1148,7 @@ extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_
   RenderParams P;
   fill_params(ctx, t, cube, disc, sh, P);
   CamConst *cams = static_cast<CamConst *>(ctx->orb_cams_dev);
-  orbit_camconst_kernel<<<1, 1024, 0, s>>>(orbits_device, n, pd, P.bw, P.bh, cams, total_dev);
+  orbit_camconst_kernel<<<1, 256, 0, s>>>(orbits_device, n, pd, P.bw, P.bh, cams, total_dev);
   count_launch(ctx);
   P.cams = cams;
   P.ncams = n;
@@ -1095,4 +1162,17 @@ extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_
   count_launch(ctx);
   BH_CUDA(cudaGetLastError());
   return BH_OK;
+}
+
+extern "C" bh_status bh_inject_fault(bh_ctx *ctx, int kind) {
+  if (!ctx) { set_error("bh_inject_fault: NULL context"); return BH_ERR_INVALID_ARG; }
+  if (kind != BH_FAULT_TABLE_WAIT) { set_error("bh_inject_fault: unknown kind %d", kind); return BH_ERR_INVALID_ARG; }
+  ctx->inject_table_wait = 1;
+  return BH_OK;
+}
+
+extern "C" bh_status bh_check_status(bh_ctx *ctx, void *stream) {
+  if (!ctx) { set_error("bh_check_status: NULL context"); return BH_ERR_INVALID_ARG; }
+  BH_CUDA(cudaSetDevice(ctx->device));
+  return check_status(ctx, (cudaStream_t)stream);
 }

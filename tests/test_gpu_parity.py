@@ -457,3 +457,23 @@ def test_render_orbits_equals_batch(ctx, gpu_tables, static_scene):
     torch.cuda.synchronize()
     for a, b in zip(outs, ref):
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6)
+
+
+def test_bounded_table_wait_reports_timeout(ctx, gpu_tables, static_scene):
+    """Failure detection without a GPU fault: the injected table wait runs out,
+    the kernel reports it through the status word, and the context renders
+    normally afterwards."""
+    cube, _ = static_scene
+    cam = synth.camera(10.0, 80.0, width=64, height=64)
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    out = torch.zeros((64, 64, 4), device="cuda")
+    assert bh.bh_check_status(ctx) == bh.BH_OK
+    bh.bh_inject_fault(ctx, bh.BH_FAULT_TABLE_WAIT)
+    bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, out)
+    with pytest.raises(bh.BhError) as ei:
+        bh.bh_check_status(ctx)
+    assert ei.value.status == bh.BH_ERR_TIMEOUT
+    ref = torch.zeros_like(out)
+    bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, ref)
+    assert bh.bh_check_status(ctx) == bh.BH_OK
+    assert float(ref[..., 3].min()) == 1.0
