@@ -64,7 +64,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "100"],
+                                          "-i", str(self.index), "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -227,6 +227,8 @@ def run_ours(args):
 
     out = torch.empty((H, W, 4), device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # tile shape for this frame size from the autotuner (untimed)
+    tuned = bh.bh_autotune_batch(ctx, tables, cube, [cam0], disc, sh, [out])
     # --- work counts for the roofline (one untimed debug render)
     dbg = torch.empty((H, W, 16), device=dev)
     bh.bh_render_debug(ctx, tables, cube, cam0, disc, sh, out, dbg, stream)
@@ -274,7 +276,7 @@ def run_ours(args):
     host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
     for s in range(2):
         bh.bh_render_to_host(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
-    e2e_steps = max(5, args.steps // 2)
+    e2e_steps = max(5, min(200, args.steps // 2))
     t = time.perf_counter()
     for s in range(e2e_steps):
         bh.bh_render_to_host(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
@@ -284,6 +286,7 @@ def run_ours(args):
     # --- served (continuous batching) and batched forms on the same frames
     served = serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=max(32, args.steps))
     batched = batch_run(bh, ctx, tables, cube, sh, dev)
+    orbits = orbit_run(bh, ctx, tables, cube, sh, dev)
     served_mixed = serve_workload(bh, dev, tables, cube, sh) if args.serve_workload else None
     if served_mixed is not None:
         # the largest per-viewer request rate whose p99 latency stays within two
@@ -308,6 +311,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(wk, ws),
         "mpix_per_s": fps * W * H / 1e6,
+        "autotune_choice": tuned,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": render_traffic(),
                      "peak_note": f"FP32 issue: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
@@ -318,7 +322,7 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "precompute_ms": {"tables_D_U_colour": precompute_ms, "cubemap_1M_stars": cubemap_ms},
-        "served": served, "batched": batched, "served_mixed": served_mixed,
+        "served": served, "batched": batched, "orbits": orbits, "served_mixed": served_mixed,
     }
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wk, seconds=12.0)
@@ -445,6 +449,44 @@ def serve_workload(bh, dev, tables, cube, sh, duration=1.5, viewers=256, rate_hz
             "mix": "720p/1080p/4K uniform; circular or radial trajectories"}
 
 
+def orbit_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
+    """64 cameras on free-fall orbits (Appendix C), resident on the device:
+    each step advances every orbit by one 60 Hz frame of proper time and
+    renders them all (camera set-up on the device, one persistent launch)."""
+    import math
+    import torch
+    from paper_2010_08735_gb300 import synth
+    rng = np.random.Generator(np.random.PCG64(5))
+    res = synth.BATCH_RESOLUTIONS
+    orbits = []
+    for _ in range(n):
+        w, h = res[int(rng.integers(len(res)))]
+        r0 = float(rng.uniform(4.0, 30.0))
+        u0 = 1.0 / r0
+        v0 = math.sqrt(u0 / (2 * (1 - u0))) * float(rng.uniform(0.9, 1.1))
+        orbits.append(bh.bh_orbit_init(r0, float(rng.uniform(1.2, 1.9)), min(v0, 0.9),
+                                       float(rng.uniform(0, math.pi)), None, math.pi / 3, w, h))
+    buf = torch.frombuffer(bytearray(bh.orbits_to_bytes(orbits)), dtype=torch.uint8).to(dev)
+    outs = [torch.empty((o.height, o.width, 4), device=dev) for o in orbits]
+    disc = synth.disc()
+    s = torch.cuda.Stream(device=dev)
+    bh.bh_orbits_advance(ctx, buf, n, 0.05, 8, s)
+    bh.bh_render_orbits(ctx, tables, cube, n, buf, disc, sh, outs, s)
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        bh.bh_orbits_advance(ctx, buf, n, 0.05, 8, s)
+        bh.bh_render_orbits(ctx, tables, cube, n, buf, disc, sh, outs, s)
+    e1.record(s)
+    s.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    px = sum(o.width * o.height for o in orbits)
+    return {"cameras": n, "ms_per_step": ms, "mpix_per_s": px / 1e6 / (ms / 1000.0),
+            "frames_1080p_equiv_per_s": px / (1920 * 1080) / (ms / 1000.0),
+            "note": "advance + on-device camera set-up + render, per step"}
+
+
 def batch_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
     """64 cameras of mixed resolution in one persistent launch; Mpix/s and
     1080p-equivalent frames/s, after the autotuner picked a tile shape."""
@@ -473,7 +515,7 @@ def batch_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

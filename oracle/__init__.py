@@ -30,7 +30,7 @@ SRC = HERE / "bh_oracle.c"
 LIB = HERE / "liboracle.so"
 
 MU = 4.0 / 27.0
-NDBG = 23
+NDBG = 25
 
 _lib = None
 
@@ -60,6 +60,7 @@ class Disc(C.Structure):
 class Scene(C.Structure):
     _fields_ = [("D", C.POINTER(C.c_double)), ("d_n", C.c_int),
                 ("U", C.POINTER(C.c_double)), ("u_ne", C.c_int), ("u_nphi", C.c_int),
+                ("DT", C.POINTER(C.c_double)), ("UT", C.POINTER(C.c_double)),
                 ("C", C.POINTER(C.c_double)), ("c_nx", C.c_int), ("c_ny", C.c_int),
                 ("c_nd", C.c_int),
                 ("disc_ln", C.POINTER(C.c_double)), ("disc_n", C.c_int),
@@ -86,6 +87,10 @@ def lib():
             "orc_u_e2_of_x": (C.c_double, [C.c_double]),
             "orc_u_phi_of_y": (C.c_double, [C.c_double, C.c_double]),
             "orc_tables_exact": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, _D, _D]),
+            "orc_tables_exact2": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D]),
+            "orc_time_of_R": (C.c_double, [C.c_double, C.c_double]),
+            "orc_trace_ray2": (None, [_D, _D, C.c_int, _D, _D, C.c_int, C.c_int, C.c_double,
+                                      C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, _D]),
             "orc_u_of_phi": (C.c_double, [C.c_double, C.c_double, C.c_double]),
             "orc_state_at_phi": (None, [C.c_double, C.c_double, C.c_double, _D]),
             "orc_apsis_deflection": (C.c_double, [C.c_double, C.c_double]),
@@ -167,6 +172,21 @@ def tables_exact(d_n: int = 512, u_ne: int = 64, u_nphi: int = 32, h0: float = 1
     return D, U
 
 
+def tables_exact_t(d_n: int = 512, u_ne: int = 64, u_nphi: int = 32, h0: float = 1e-3):
+    """As tables_exact, plus the regularised time channels R = t + 1/u -
+    ln(u/(1-u)) of D and U (same layouts): returns D, U, DT, UT."""
+    D = np.zeros((d_n, d_n)); U = np.zeros((u_nphi, u_ne))
+    DT = np.zeros((d_n, d_n)); UT = np.zeros((u_nphi, u_ne))
+    rc = lib().orc_tables_exact2(d_n, u_ne, u_nphi, h0, _dp(D), _dp(U), _dp(DT), _dp(UT))
+    if rc:
+        raise ValueError(f"orc_tables_exact2 failed ({rc})")
+    return D, U, DT, UT
+
+
+def time_of_R(R: float, u: float) -> float:
+    return lib().orc_time_of_R(R, u)
+
+
 def u_of_phi(e2: float, phi: float, h0: float = 1e-4) -> float:
     return lib().orc_u_of_phi(e2, phi, h0)
 
@@ -196,10 +216,21 @@ def trace_ray(D, U, pr, delta, alpha, u_ic, u_oc, alpha_valid=True):
     """Algorithm 1 TRACERAY.  Returns dict(delta_p, hits=[(u, angle)], e2)."""
     D = np.ascontiguousarray(D, dtype=np.float64)
     U = np.ascontiguousarray(U, dtype=np.float64)
-    o = np.zeros(8)
+    o = np.zeros(10)
     lib().orc_trace_ray(_dp(D), D.shape[0], _dp(U), U.shape[1], U.shape[0], pr, delta, alpha,
                         int(alpha_valid), u_ic, u_oc, _dp(o))
     hits = [(o[2 + 2 * k], o[3 + 2 * k]) for k in range(int(o[1]))]
+    return {"delta_p": o[0], "hits": hits, "e2": o[6]}
+
+
+def trace_ray_t(D, DT, U, UT, pr, delta, alpha, u_ic, u_oc, alpha_valid=True):
+    """TRACERAY with the retarded times of the hits (camera time minus emission)."""
+    arr = [np.ascontiguousarray(a, dtype=np.float64) for a in (D, DT, U, UT)]
+    o = np.zeros(10)
+    lib().orc_trace_ray2(_dp(arr[0]), _dp(arr[1]), arr[0].shape[0], _dp(arr[2]), _dp(arr[3]),
+                         arr[2].shape[1], arr[2].shape[0], pr, delta, alpha, int(alpha_valid), u_ic,
+                         u_oc, _dp(o))
+    hits = [(o[2 + 2 * k], o[3 + 2 * k], o[8 + k]) for k in range(int(o[1]))]
     return {"delta_p": o[0], "hits": hits, "e2": o[6]}
 
 
@@ -327,9 +358,11 @@ def disc_temperature(t_peak, u) -> float:
 class SceneTables:
     """Stored tables, dequantised to double, that a render reads."""
 
-    def __init__(self, D, U, Ct, disc_ln, cube=None, cube_n=0, cube_dtype=1):
+    def __init__(self, D, U, Ct, disc_ln, cube=None, cube_n=0, cube_dtype=1, DT=None, UT=None):
         self.D = np.ascontiguousarray(D, dtype=np.float64)
         self.U = np.ascontiguousarray(U, dtype=np.float64)
+        self.DT = None if DT is None else np.ascontiguousarray(DT, dtype=np.float64)
+        self.UT = None if UT is None else np.ascontiguousarray(UT, dtype=np.float64)
         self.C = np.ascontiguousarray(Ct, dtype=np.float64)
         self.disc_ln = np.ascontiguousarray(disc_ln, dtype=np.float64)
         self.cube = None if cube is None else np.ascontiguousarray(cube, dtype=np.uint16)
@@ -340,6 +373,8 @@ class SceneTables:
         s = Scene()
         s.D, s.d_n = _dp(self.D), self.D.shape[0]
         s.U, s.u_ne, s.u_nphi = _dp(self.U), self.U.shape[1], self.U.shape[0]
+        if self.DT is not None and self.UT is not None:
+            s.DT, s.UT = _dp(self.DT), _dp(self.UT)
         s.C = _dp(self.C)
         s.c_nd, s.c_ny, s.c_nx = self.C.shape[0], self.C.shape[1], self.C.shape[2]
         s.disc_ln, s.disc_n = _dp(self.disc_ln), self.disc_ln.shape[0]

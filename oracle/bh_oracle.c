@@ -63,6 +63,27 @@ static void rk4_step(double u, double ud, double h, double *uo, double *udo) {
   *udo = ud + h / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
 }
 
+/* The same step carrying the regularised time R = t + 1/u - ln(u/(1-u)) of
+ * the ray: with dt/dphi = e/(u^2 (1-u)) (Eq. motionconstants) and the first
+ * integral (du/dphi)^2 = e^2 - u^2 (1-u), dR/dphi = 1/(e + du/dphi), finite
+ * from u = 0 (where R = 0) through the apsis up to phi < pi. */
+static void rk4_step_t(double e, double u, double ud, double R, double h, double *uo, double *udo,
+                       double *Ro) {
+  double k1u = ud, k1v = accel(u), k1r = 1.0 / (e + ud);
+  double u2 = u + 0.5 * h * k1u, v2 = ud + 0.5 * h * k1v;
+  double k2u = v2, k2v = accel(u2), k2r = 1.0 / (e + v2);
+  double u3 = u + 0.5 * h * k2u, v3 = ud + 0.5 * h * k2v;
+  double k3u = v3, k3v = accel(u3), k3r = 1.0 / (e + v3);
+  double u4 = u + h * k3u, v4 = ud + h * k3v;
+  double k4u = v4, k4v = accel(u4), k4r = 1.0 / (e + v4);
+  *uo = u + h / 6.0 * (k1u + 2.0 * k2u + 2.0 * k3u + k4u);
+  *udo = ud + h / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+  *Ro = R + h / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+}
+
+/* Coordinate time from the regularised time: t = R - 1/u + ln(u/(1-u)). */
+double orc_time_of_R(double R, double u) { return R - 1.0 / u + log(u / (1.0 - u)); }
+
 /* Apsis of a scattered ray, Eq. uapsis (valid for e^2 < mu). */
 double orc_apsis(double e2) {
   return 1.0 / 3.0 + 2.0 / 3.0 * sin(asin(2.0 * e2 / MU - 1.0) / 3.0);
@@ -131,15 +152,15 @@ static double solve_step_for_apsis(double u, double ud, double smax) {
  * coordinates y_j = j/(n-1) of the Appendix A mapping (reading C3: the first
  * and last texels hold the ends of the [0,1] range, so y = 1 is the apsis or
  * the horizon exactly).  out[j*stride]. */
-static void d_column(double e2, int n, double h0, double *out, int stride) {
+static void d_column(double e2, int n, double h0, double *out, double *outR, int stride) {
   double e = sqrt(e2);
   double h = h0 / (e > 1.0 ? e : 1.0);
-  double u = 0.0, ud = e, phi = 0.0;
+  double u = 0.0, ud = e, phi = 0.0, R = 0.0;
   int j = 0;
   double target = orc_d_u_of_y(e2, 0.0);
   while (j < n) {
-    double u1, ud1;
-    rk4_step(u, ud, h, &u1, &ud1);
+    double u1, ud1, R1;
+    rk4_step_t(e, u, ud, R, h, &u1, &ud1, &R1);
     if (e2 < MU && ud1 <= 0.0) {
       /* The apsis lies inside this step: the remaining texels are between
        * the current point and the apsis, where u increases. */
@@ -149,10 +170,11 @@ static void d_column(double e2, int n, double h0, double *out, int stride) {
       while (j < n) {
         /* y = 1 is the apsis itself; elsewhere find u(s) = target */
         double s = (j == n - 1 || target > ua) ? sa : solve_step_for_u(u, ud, sa, target);
-        double us, uds;
-        rk4_step(u, ud, s, &us, &uds);
+        double us, uds, Rs;
+        rk4_step_t(e, u, ud, R, s, &us, &uds, &Rs);
         if (uds < 0.0) uds = 0.0;
         out[(long)j * stride] = phi + s - atan2(us, uds);
+        if (outR) outR[(long)j * stride] = Rs;
         ++j;
         if (j < n) target = orc_d_u_of_y(e2, (double)j / (n - 1));
       }
@@ -160,13 +182,14 @@ static void d_column(double e2, int n, double h0, double *out, int stride) {
     }
     while (j < n && target <= u1) {
       double s = solve_step_for_u(u, ud, h, target);
-      double us, uds;
-      rk4_step(u, ud, s, &us, &uds);
+      double us, uds, Rs;
+      rk4_step_t(e, u, ud, R, s, &us, &uds, &Rs);
       out[(long)j * stride] = phi + s - atan2(us, uds);
+      if (outR) outR[(long)j * stride] = Rs;
       ++j;
       if (j < n) target = orc_d_u_of_y(e2, (double)j / (n - 1));
     }
-    u = u1; ud = ud1; phi += h;
+    u = u1; ud = ud1; R = R1; phi += h;
   }
 }
 
@@ -174,23 +197,28 @@ static void d_column(double e2, int n, double h0, double *out, int stride) {
  * texel coordinates y_j = j/(n-1), or 1 once the ray has reached the horizon
  * u = 1 (reading C7).  Algorithm 1 writes U for phi < pi only; every texel of
  * the Appendix A mapping has phi < pi. */
-static void u_column(double e2, int n, double h0, double *out, int stride) {
+static void u_column(double e2, int n, double h0, double *out, double *outR, int stride) {
   double e = sqrt(e2);
   double h = h0 / (e > 1.0 ? e : 1.0);
-  double u = 0.0, ud = e, phi = 0.0;
+  double u = 0.0, ud = e, phi = 0.0, R = 0.0;
   int captured = 0;
   for (int j = 0; j < n; ++j) {
     double phij = orc_u_phi_of_y(e2, (double)j / (n - 1));
     while (!captured && phi + h <= phij) {
-      double u1, ud1;
-      rk4_step(u, ud, h, &u1, &ud1);
-      u = u1; ud = ud1; phi += h;
+      double u1, ud1, R1;
+      rk4_step_t(e, u, ud, R, h, &u1, &ud1, &R1);
+      u = u1; ud = ud1; R = R1; phi += h;
       if (u >= 1.0) captured = 1;
     }
-    if (captured) { out[(long)j * stride] = 1.0; continue; }
-    double us, uds;
-    rk4_step(u, ud, phij - phi, &us, &uds);
+    if (captured) {
+      out[(long)j * stride] = 1.0;
+      if (outR) outR[(long)j * stride] = 0.0;
+      continue;
+    }
+    double us, uds, Rs;
+    rk4_step_t(e, u, ud, R, phij - phi, &us, &uds, &Rs);
     out[(long)j * stride] = us >= 1.0 ? 1.0 : us;
+    if (outR) outR[(long)j * stride] = us >= 1.0 ? 0.0 : Rs;
   }
 }
 
@@ -198,19 +226,36 @@ static void u_column(double e2, int n, double h0, double *out, int stride) {
  * indexes u (y).  U: u_nphi x u_ne doubles, U[j*u_ne + i], i indexes e, j
  * indexes phi.  Texel i of n holds coordinate i/(n-1) (reading C3).  h0 is
  * the RK4 step in phi (scaled down by e for e > 1).  U's column x = 0 is the
- * limit e -> infinity, a radial ray, captured at once (u = 1 for phi > 0). */
-int orc_tables_exact(int d_n, int u_ne, int u_nphi, double h0, double *D, double *U) {
+ * limit e -> infinity, a radial ray, captured at once (u = 1 for phi > 0).
+ * DT, UT (may be NULL): the regularised time R = t + 1/u - ln(u/(1-u)) of the
+ * same texels (reading C5); 0 where u = 0 or the ray is captured. */
+int orc_tables_exact2(int d_n, int u_ne, int u_nphi, double h0, double *D, double *U, double *DT,
+                      double *UT) {
   if (d_n < 4 || (d_n & 1) || u_ne < 2 || u_nphi < 2 || !(h0 > 0.0)) return 1;
   for (int i = 0; i < d_n; ++i) {
     double e2 = orc_d_e2_of_x((double)i / (d_n - 1));
-    d_column(e2, d_n, h0, D + i, d_n);
+    d_column(e2, d_n, h0, D + i, DT ? DT + i : NULL, d_n);
   }
-  for (int j = 0; j < u_nphi; ++j) U[(long)j * u_ne] = j == 0 ? 0.0 : 1.0;
+  for (int j = 0; j < u_nphi; ++j) {
+    U[(long)j * u_ne] = j == 0 ? 0.0 : 1.0;
+    if (UT) UT[(long)j * u_ne] = 0.0;
+  }
   for (int i = 1; i < u_ne; ++i) {
     double e2 = orc_u_e2_of_x((double)i / (u_ne - 1));
-    u_column(e2, u_nphi, h0, U + i, u_ne);
+    if (e2 <= 0.0) { /* e = 0: no ray */
+      for (int j = 0; j < u_nphi; ++j) {
+        U[(long)j * u_ne + i] = 0.0;
+        if (UT) UT[(long)j * u_ne + i] = 0.0;
+      }
+      continue;
+    }
+    u_column(e2, u_nphi, h0, U + i, UT ? UT + i : NULL, u_ne);
   }
   return 0;
+}
+
+int orc_tables_exact(int d_n, int u_ne, int u_nphi, double h0, double *D, double *U) {
+  return orc_tables_exact2(d_n, u_ne, u_nphi, h0, D, U, NULL, NULL);
 }
 
 /* u(phi) on the ray from infinity with constant e (RK4, step h0); 1 once
@@ -318,21 +363,30 @@ double orc_u_lookup(const double *U, int ne, int nphi, double e2, double phi) {
 /*      post-apsis hit only (see below).                                      */
 /* Hits are returned in the order met along the backward ray.                 */
 /* ------------------------------------------------------------------------ */
-void orc_trace_ray(const double *D, int dn, const double *U, int une, int unphi,
-                   double pr, double delta, double alpha, int alpha_valid,
-                   double u_ic, double u_oc, double *out) {
+void orc_trace_ray2(const double *D, const double *DT, int dn, const double *U, const double *UT,
+                    int une, int unphi, double pr, double delta, double alpha, int alpha_valid,
+                    double u_ic, double u_oc, double *out) {
   double u = 1.0 / pr;
   double ud = -u * cos(delta) / sin(delta); /* du/dphi = -u cot(delta) */
   double e2 = ud * ud + u * u * (1.0 - u);
   out[0] = INFINITY; out[1] = 0; out[2] = 0; out[3] = 0; out[4] = 0; out[5] = 0;
-  out[6] = e2; out[7] = 0;
+  out[6] = e2; out[7] = 0; out[8] = 0; out[9] = 0;
   if (e2 < MU && u > 2.0 / 3.0) return; /* trapped inside the photon sphere */
   int s = ud > 0.0 ? 1 : -1;
   double Dl = orc_d_lookup(D, dn, e2, u);
   double Da = 0.0, phia = INFINITY;           /* reading C6: no apsis if e^2 >= mu */
+  double ua = 0.0;
   if (e2 < MU) {
-    Da = orc_d_lookup(D, dn, e2, orc_apsis(e2));
+    ua = orc_apsis(e2);
+    Da = orc_d_lookup(D, dn, e2, ua);
     phia = Da + PI / 2.0;
+  }
+  /* retarded times (Algorithm 1): coordinate time of the camera point and of
+   * the apsis on the ray from infinity, from the regularised time channel */
+  double tc = 0.0, ta = 0.0;
+  if (DT) {
+    tc = orc_time_of_R(orc_d_lookup(DT, dn, e2, u), u);
+    if (e2 < MU) ta = orc_time_of_R(orc_d_lookup(DT, dn, e2, ua), ua);
   }
   int nh = 0;
   if (alpha_valid) {
@@ -343,6 +397,7 @@ void orc_trace_ray(const double *D, int dn, const double *U, int une, int unphi,
         ((s == 1 && u0 > u) || (s == -1 && u0 < u))) {
       out[2 + 2 * nh] = u0;
       out[3 + 2 * nh] = alpha + phi - phi0;
+      if (UT) out[8 + nh] = s * (orc_time_of_R(orc_u_lookup(UT, une, unphi, e2, phi0), u0) - tc);
       ++nh;
     }
     if (e2 < MU && s == 1) {
@@ -352,6 +407,7 @@ void orc_trace_ray(const double *D, int dn, const double *U, int une, int unphi,
       if (phi1 < phia && u_oc <= u1 && u1 <= u_ic) {
         out[2 + 2 * nh] = u1;
         out[3 + 2 * nh] = alpha + phi - phi1;
+        if (UT) out[8 + nh] = 2.0 * ta - tc - orc_time_of_R(orc_u_lookup(UT, une, unphi, e2, phi1), u1);
         ++nh;
       }
     }
@@ -360,6 +416,13 @@ void orc_trace_ray(const double *D, int dn, const double *U, int une, int unphi,
   double Delta = Dl;
   if (ud > 0.0) Delta = e2 < MU ? 2.0 * Da - Dl : INFINITY;
   out[0] = delta + Delta;
+}
+
+/* TRACERAY without the time channels; out as orc_trace_ray2 (10 doubles). */
+void orc_trace_ray(const double *D, int dn, const double *U, int une, int unphi, double pr,
+                   double delta, double alpha, int alpha_valid, double u_ic, double u_oc,
+                   double *out) {
+  orc_trace_ray2(D, NULL, dn, U, NULL, une, unphi, pr, delta, alpha, alpha_valid, u_ic, u_oc, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -786,6 +849,7 @@ typedef struct {
 typedef struct {
   const double *D; int d_n;
   const double *U; int u_ne, u_nphi;
+  const double *DT, *UT; /* regularised time channels (may be NULL) */
   const double *C; int c_nx, c_ny, c_nd;
   const double *disc_ln; int disc_n;
   const uint16_t *cube; int cube_n, cube_dtype;
@@ -924,7 +988,7 @@ double orc_disc_temperature(double t_peak, double u) {
 /* Per-pixel render                                                          */
 /* ------------------------------------------------------------------------ */
 
-#define NDBG 23
+#define NDBG 25
 typedef struct {
   const orc_camera *cam;
   const orc_disc *disc;
@@ -942,7 +1006,7 @@ typedef struct {
   beam b;
   double dprime[3];
   int captured;
-  double tr[8];
+  double tr[10];
 } pix;
 
 static void trace_pixel(render_job *J, int i, int j, pix *p) {
@@ -950,8 +1014,8 @@ static void trace_pixel(render_job *J, int i, int j, pix *p) {
   double qw = i + 0.5 - 0.5 * c->width, qh = 0.5 * c->height - j - 0.5;
   beam_init(c, &J->F, qw, qh, &p->b);
   double uic = 1.0 / J->disc->r_in, uoc = 1.0 / J->disc->r_out;
-  orc_trace_ray(J->sc->D, J->sc->d_n, J->sc->U, J->sc->u_ne, J->sc->u_nphi, c->r, p->b.delta,
-                p->b.alpha, p->b.alpha_valid && J->disc->enabled, uic, uoc, p->tr);
+  orc_trace_ray2(J->sc->D, J->sc->DT, J->sc->d_n, J->sc->U, J->sc->UT, J->sc->u_ne, J->sc->u_nphi,
+                 c->r, p->b.delta, p->b.alpha, p->b.alpha_valid && J->disc->enabled, uic, uoc, p->tr);
   p->captured = isinf(p->tr[0]);
   if (!p->captured) {
     double cd = cos(p->tr[0]), sd = sin(p->tr[0]);
@@ -1083,6 +1147,8 @@ static void render_pixel(render_job *J, int i, int j, pix *quad[2][2], double *o
   d[3] = P->tr[1];
   d[4] = P->tr[2];
   d[5] = P->tr[4];
+  d[23] = P->tr[8]; /* retarded time (camera minus emission) of hit slot 0 */
+  d[24] = P->tr[9];
   /* disc hits, front to back (Sec. 3.3.3, reading C13) */
   double L[3] = {0, 0, 0};
   double trans = 1.0;
@@ -1173,7 +1239,7 @@ static void *render_worker(void *argp) {
  *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|),
  *  19 |gradient| of the star sum's Y per pixel of footprint shift, relative
  *     to that sum, 20..22 resulting bound on the change of R, G, B per pixel
- *     of footprint shift.
+ *     of footprint shift, 23..24 retarded times of the two hit slots.
  * force_level >= 0 forces the mip level (for the flat-space checks). */
 int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc,
                double exposure_stars, const orc_scene *sc, int y0, int y1, int force_level,

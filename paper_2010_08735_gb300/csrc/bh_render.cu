@@ -477,50 +477,17 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
             SY = fmaf(wt, Y, SY);
             SZ = fmaf(wt, Z, SZ);
           };
-          const int nrows = j1 - j0 + 1;
           const bool straddle = b0 + nrow > 32 && w0i + 1 < wpr;
-          if (nrows > 0 && nrow > 0) visited += nrows * nrow;
-          if (nrows <= 10 && nrow <= 10) {
-            // all rows' occupancy bits first (independent loads), packed as
-            // bit 10 r + k for row j0 + r, column i0 + k; then the set bits
-            unsigned long long lo = 0ull, hi = 0ull;
-#pragma unroll
-            for (int rr = 0; rr < 10; ++rr) {
-              if (rr < nrows) {
-                const unsigned *mrow = mrows + (long long)(j0 + rr) * wpr + w0i;
-                unsigned long long win = __ldg(mrow);
-                if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
-                const unsigned long long bits = (win >> b0) & rowbits;
-                const int off = 10 * rr;
-                if (off < 64) {
-                  lo |= bits << off;
-                  if (off + 10 > 64) hi |= bits >> (64 - off);
-                } else {
-                  hi |= bits << (off - 64);
-                }
-              }
-            }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              unsigned long long m = half ? hi : lo;
-              while (m) {
-                const int idx = __ffsll((long long)m) - 1 + 64 * half;
-                m &= m - 1ull;
-                const int rr = idx / 10;
-                take(j0 + rr, idx - 10 * rr);
-              }
-            }
-          } else {
-            for (int jj = j0; jj <= j1; ++jj) {  // rounding at the level edge
-              const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
-              unsigned long long win = __ldg(mrow);
-              if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
-              unsigned bits = (unsigned)(win >> b0) & rowbits;
-              while (bits) {
-                const int k = __ffs(bits) - 1;
-                bits &= bits - 1u;
-                take(jj, k);
-              }
+          for (int jj = j0; jj <= j1; ++jj) {
+            const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
+            unsigned long long win = __ldg(mrow);
+            if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
+            unsigned bits = (unsigned)(win >> b0) & rowbits;
+            if (nrow > 0) visited += nrow;
+            while (bits) {
+              const int k = __ffs(bits) - 1;
+              bits &= bits - 1u;
+              take(jj, k);
             }
           }
         }
@@ -1026,8 +993,9 @@ extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh
   if (st) return st;
   BH_CUDA(cudaSetDevice(ctx->device));
   // candidates: warps per block, block tile width, resident blocks per SM
-  static const RenderTuning cand[] = {{8, 32, 4}, {8, 16, 4}, {8, 64, 4}, {4, 32, 8},
-                                      {4, 16, 8}, {8, 32, 2}, {8, 32, 8}, {8, 8, 4}};
+  static const RenderTuning cand[] = {{8, 32, 4}, {8, 16, 4}, {8, 64, 4},  {4, 32, 8},
+                                      {4, 16, 8}, {8, 32, 2}, {8, 32, 8},  {8, 8, 4},
+                                      {8, 32, 16}, {8, 16, 8}, {8, 16, 16}, {4, 32, 16}};
   const int nc = sizeof(cand) / sizeof(cand[0]);
   cudaStream_t s;
   BH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
