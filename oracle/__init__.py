@@ -89,6 +89,7 @@ def lib():
             "orc_tables_exact": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, _D, _D]),
             "orc_tables_exact2": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D]),
             "orc_time_of_R": (C.c_double, [C.c_double, C.c_double]),
+            "orc_time_at_phi": (None, [C.c_double, C.c_double, C.c_double, _D]),
             "orc_trace_ray2": (None, [_D, _D, C.c_int, _D, _D, C.c_int, C.c_int, C.c_double,
                                       C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, _D]),
             "orc_u_of_phi": (C.c_double, [C.c_double, C.c_double, C.c_double]),
@@ -185,6 +186,13 @@ def tables_exact_t(d_n: int = 512, u_ne: int = 64, u_nphi: int = 32, h0: float =
 
 def time_of_R(R: float, u: float) -> float:
     return lib().orc_time_of_R(R, u)
+
+
+def time_at_phi(e2: float, phi: float, h0: float = 1e-4):
+    """(u, du/dphi, R, t) at angle phi on the ray from infinity."""
+    o = np.zeros(4)
+    lib().orc_time_at_phi(e2, phi, h0, _dp(o))
+    return tuple(o)
 
 
 def u_of_phi(e2: float, phi: float, h0: float = 1e-4) -> float:

@@ -292,6 +292,21 @@ double orc_apsis_deflection(double e2, double h0) {
   }
 }
 
+/* Coordinate time t(phi) on the ray from infinity, from the regularised time
+ * (RK4, step h0): out[0] = u, out[1] = du/dphi, out[2] = R, out[3] = t. */
+void orc_time_at_phi(double e2, double phi, double h0, double *out) {
+  double e = sqrt(e2);
+  double h = h0 / (e > 1.0 ? e : 1.0);
+  double u = 0.0, ud = e, R = 0.0, p = 0.0;
+  while (p + h <= phi) {
+    double u1, ud1, R1;
+    rk4_step_t(e, u, ud, R, h, &u1, &ud1, &R1);
+    u = u1; ud = ud1; R = R1; p += h;
+  }
+  rk4_step_t(e, u, ud, R, phi - p, &out[0], &out[1], &out[2]);
+  out[3] = orc_time_of_R(out[2], out[0]);
+}
+
 /* State (u, du/dphi) after integrating to angle phi (for the first-integral
  * check).  out[0] = u, out[1] = du/dphi. */
 void orc_state_at_phi(double e2, double phi, double h0, double *out) {
