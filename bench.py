@@ -230,10 +230,10 @@ def run_ours(args):
     # tile shape for this frame size from the autotuner (untimed)
     tuned = bh.bh_autotune_batch(ctx, tables, cube, [cam0], disc, sh, [out])
     # --- work counts for the roofline (one untimed debug render)
-    dbg = torch.empty((H, W, 16), device=dev)
+    dbg = torch.empty((H, W, bh.NDBG), device=dev)
     bh.bh_render_debug(ctx, tables, cube, cam0, disc, sh, out, dbg, stream)
     stream.synchronize()
-    d = dbg.view(-1, 16)
+    d = dbg.view(-1, bh.NDBG)
     texels = float(d[:, 15].sum().item())
     hits = float(d[:, 3].sum().item())
     del dbg, d
@@ -515,7 +515,7 @@ def batch_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -119,6 +119,21 @@ bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, const double 
  * device. */
 bh_status bh_tables_copy_out(const bh_tables *t, double *D_host, double *U_host);
 
+/* Retarded-time channels of D and U (Algorithm 1 stores the coordinate time
+ * t beside Delta and u).  Both hold the regularised time
+ *     R = t + 1/u - ln(u / (1 - u)),   dR/dphi = 1 / (e + du/dphi),
+ * with t = 0 at phi = 0 (the ray's start at infinity), finite everywhere on
+ * the tables (t itself diverges at u = 0 and at the horizon).  DT has D's
+ * layout and texel coordinates; UT has U's, 0 where the ray was captured or
+ * does not exist.  Past the apsis UT follows from t(phi) = 2 t_a -
+ * t(2 phi_a - phi).  bh_precompute_tables fills them; after bh_tables_upload
+ * they are NaN until bh_tables_upload_time sets them from host FP64 values
+ * (same layouts; synchronises `stream`).  bh_tables_copy_time copies them
+ * out (either pointer may be NULL; synchronises the device). */
+bh_status bh_tables_upload_time(bh_tables *t, const double *DT_host, const double *UT_host,
+                                void *stream);
+bh_status bh_tables_copy_time(const bh_tables *t, double *DT_host, double *UT_host);
+
 /* Copy the colour tables: C as [log2 D][y][x] float4 (XYZ, pad), 64*32*64*4
  * floats; the disc black-body table as 1024 float4 (ln Y, X/Y, Z/Y, pad) at
  * log2 T = 8 + 12 (k + 1/2)/1024.  Either may be NULL.  Synchronises. */
@@ -208,11 +223,13 @@ bh_status bh_render(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cube
                     const bh_camera *camera, const bh_disc *disc, const bh_shading *shading,
                     float *out_rgba_device, void *stream);
 
-/* As bh_render, plus 16 floats per pixel of intermediate values in
- * dbg_device: e^2, delta, delta' (+inf if captured), number of disc hits,
- * u0, u1, mip level (-1: no star term), cube face, Omega/Omega', star
- * Doppler factor, gathered star X, Y, Z, hit-0 Doppler, hit-1 Doppler,
- * texels visited. */
+/* As bh_render, plus 20 floats per pixel of intermediate values in
+ * dbg_device (16-byte aligned): e^2, delta, delta' (+inf if captured),
+ * number of disc hits, u0, u1, mip level (-1: no star term), cube face,
+ * Omega/Omega', star Doppler factor, gathered star X, Y, Z, hit-0 Doppler,
+ * hit-1 Doppler, texels visited, then the retarded-time delays of hits 0
+ * and 1 (coordinate time from the disc point to the camera along the beam,
+ * from the tables' time channels; 0 without a hit) and two zeros. */
 bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
                           const bh_camera *camera, const bh_disc *disc,
                           const bh_shading *shading, float *out_rgba_device, float *dbg_device,
@@ -232,7 +249,7 @@ bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap
                           const bh_camera *cameras, const bh_disc *disc,
                           const bh_shading *shading, float *const *outs, void *stream);
 
-/* Autotuning of the batched launch: time the candidate tile shapes on the
+/* Autotuning of the batched launch: time the candidate launch shapes on the
  * given cameras (renders them several times, synchronously) and keep the
  * fastest for later bh_render_batch calls of this context.  *chosen receives
  * the chosen candidate index (may be NULL). */

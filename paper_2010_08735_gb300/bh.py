@@ -22,7 +22,7 @@ BH_F32, BH_F16, BH_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "BH_OK", 1: "BH_ERR_INVALID_ARG", 2: "BH_ERR_CUDA", 3: "BH_ERR_OOM",
                 4: "BH_ERR_BUSY", 5: "BH_ERR_NOT_READY", 6: "BH_ERR_TIMEOUT",
                 7: "BH_ERR_DEVICE_STATUS"}
-NDBG = 16
+NDBG = 20
 
 
 class BhError(RuntimeError):
@@ -80,6 +80,8 @@ def lib():
             "bh_precompute_tables": [_vp, P(TableDesc), _vp, P(_vp)],
             "bh_tables_upload": [_vp, P(TableDesc), P(C.c_double), P(C.c_double), _vp, P(_vp)],
             "bh_tables_copy_out": [_vp, P(C.c_double), P(C.c_double)],
+            "bh_tables_upload_time": [_vp, P(C.c_double), P(C.c_double), _vp],
+            "bh_tables_copy_time": [_vp, P(C.c_double), P(C.c_double)],
             "bh_tables_copy_colour": [_vp, P(C.c_float), P(C.c_float)],
             "bh_build_star_cubemap": [_vp, _vp, C.c_longlong, C.c_int, C.c_int, C.c_int, _vp,
                                       P(_vp)],
@@ -247,6 +249,22 @@ def bh_tables_copy_out(tables: int, d_n: int, u_ne: int, u_nphi: int):
     _check(lib().bh_tables_copy_out(tables, D.ctypes.data_as(C.POINTER(C.c_double)),
                                     U.ctypes.data_as(C.POINTER(C.c_double))))
     return D, U
+
+
+def bh_tables_upload_time(tables: int, DT: np.ndarray, UT: np.ndarray, stream=None) -> None:
+    DT = np.ascontiguousarray(DT, dtype=np.float64)
+    UT = np.ascontiguousarray(UT, dtype=np.float64)
+    _check(lib().bh_tables_upload_time(tables, DT.ctypes.data_as(C.POINTER(C.c_double)),
+                                       UT.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+
+
+def bh_tables_copy_time(tables: int, d_n: int, u_ne: int, u_nphi: int):
+    """Regularised-time channels (DT, UT), same layouts as D and U."""
+    DT = np.zeros((d_n, d_n))
+    UT = np.zeros((u_nphi, u_ne))
+    _check(lib().bh_tables_copy_time(tables, DT.ctypes.data_as(C.POINTER(C.c_double)),
+                                     UT.ctypes.data_as(C.POINTER(C.c_double))))
+    return DT, UT
 
 
 def bh_tables_copy_colour(tables: int):

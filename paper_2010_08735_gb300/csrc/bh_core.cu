@@ -108,51 +108,70 @@ __device__ __forceinline__ double qw(const Apsis &a, double w) {
   return a.A + a.B * w2 - w2 * w2;
 }
 
-// int_{w0}^{w1} 2 dw / sqrt(q(w)), composite Gauss-Legendre
-__device__ double quad_w(const Apsis &a, double w0, double w1, int panels) {
+// The regularised time R = t + 1/u - ln(u/(1-u)) (reading C5) obeys
+// dR/dphi = 1/(e + du/dphi), so every angle quadrature below has a time twin
+// (TIME = true) whose integrand carries the extra factor 1/(e + du/dphi).
+
+// int_{w0}^{w1} 2 dw / sqrt(q(w)) [/(e + w sqrt(q))], composite Gauss-Legendre
+template <bool TIME>
+__device__ double quad_w(const Apsis &a, double e, double w0, double w1, int panels) {
   double h = (w1 - w0) / panels, s = 0.0;
   for (int p = 0; p < panels; ++p) {
     double c = w0 + (p + 0.5) * h, r = 0.5 * h;
-    for (int k = 0; k < kGL; ++k) s += cGLw[k] * r * 2.0 * rsqrt(qw(a, c + r * cGLx[k]));
-  }
-  return s;
-}
-
-// same integral in t, w = c sinh t, c = sqrt(A/B): integrand 2 c cosh t / sqrt(q)
-__device__ double quad_t_scatter(const Apsis &a, double c, double t0, double t1, int panels) {
-  double h = (t1 - t0) / panels, s = 0.0;
-  for (int p = 0; p < panels; ++p) {
-    double m = t0 + (p + 0.5) * h, r = 0.5 * h;
     for (int k = 0; k < kGL; ++k) {
-      double t = m + r * cGLx[k];
-      double sh = sinh(t);
-      s += cGLw[k] * r * 2.0 * c * sqrt(1.0 + sh * sh) * rsqrt(qw(a, c * sh));
+      double w = c + r * cGLx[k], q = qw(a, w), rq = rsqrt(q);
+      double f = 2.0 * rq;
+      if (TIME) f /= e + w * q * rq;
+      s += cGLw[k] * r * f;
     }
   }
   return s;
 }
 
-// Phi(w0) = int_{w0}^{sqrt(u_a)} 2 dw / sqrt(q): angle from infinity to u = u_a - w0^2.
-__device__ double phi_scatter(const Apsis &a, double w0) {
+// same integral in t, w = c sinh t, c = sqrt(A/B): integrand 2 c cosh t / sqrt(q)
+template <bool TIME>
+__device__ double quad_t_scatter(const Apsis &a, double e, double c, double t0, double t1, int panels) {
+  double h = (t1 - t0) / panels, s = 0.0;
+  for (int p = 0; p < panels; ++p) {
+    double m = t0 + (p + 0.5) * h, r = 0.5 * h;
+    for (int k = 0; k < kGL; ++k) {
+      double t = m + r * cGLx[k];
+      double sh = sinh(t), w = c * sh, q = qw(a, w), rq = rsqrt(q);
+      double f = 2.0 * c * sqrt(1.0 + sh * sh) * rq;
+      if (TIME) f /= e + w * q * rq;
+      s += cGLw[k] * r * f;
+    }
+  }
+  return s;
+}
+
+// From infinity to u = u_a - w0^2: the angle (TIME = false) or the
+// regularised time (TIME = true), int_{w0}^{sqrt(u_a)} in w.
+template <bool TIME>
+__device__ double scatter_integral(const Apsis &a, double e, double w0) {
   double w1 = sqrt(a.ua);
   if (a.ua > 0.6) {
     double c = sqrt(a.A / a.B);
     double wm = fmax(w0, fmin(w1, 0.35));
-    return quad_t_scatter(a, c, asinh(w0 / c), asinh(wm / c), 6) + quad_w(a, wm, w1, 4);
+    return quad_t_scatter<TIME>(a, e, c, asinh(w0 / c), asinh(wm / c), 6) + quad_w<TIME>(a, e, wm, w1, 4);
   }
-  return quad_w(a, w0, w1, 4);
+  return quad_w<TIME>(a, e, w0, w1, 4);
 }
 
-// Plunging rays: int_{ta}^{tb} dt / sqrt(1 + v tanh^2 t), v = se sinh t.
-__device__ double phi_plunge(double se, double ta, double tb) {
+// Plunging rays: int_{ta}^{tb} dt / sqrt(1 + v tanh^2 t), v = se sinh t
+// (du/dphi = se cosh t sqrt(1 + v tanh^2 t)).
+template <bool TIME>
+__device__ double plunge_integral(double se, double e, double ta, double tb) {
   const int panels = 6;
   double h = (tb - ta) / panels, s = 0.0;
   for (int p = 0; p < panels; ++p) {
     double m = ta + (p + 0.5) * h, r = 0.5 * h;
     for (int k = 0; k < kGL; ++k) {
       double t = m + r * cGLx[k];
-      double th = tanh(t);
-      s += cGLw[k] * r * rsqrt(1.0 + se * sinh(t) * th * th);
+      double th = tanh(t), g = 1.0 + se * sinh(t) * th * th, rg = rsqrt(g);
+      double f = rg;
+      if (TIME) f /= e + se * cosh(t) * g * rg;
+      s += cGLw[k] * r * f;
     }
   }
   return s;
@@ -168,22 +187,24 @@ __device__ __forceinline__ __half to_storage<__half>(double v) { return __double
 // D(e,u) per texel: texel (i,j) holds the Appendix A coordinates
 // x = i/(n-1), y = j/(n-1) (reading C3).
 template <typename T>
-__global__ void precompute_D_kernel(int n, double *D64, T *Ds) {
+__global__ void precompute_D_kernel(int n, double *D64, T *Ds, double *DT64, float *DTs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
   if (i >= n || j >= n) return;
   double x = (double)i / (n - 1), y = (double)j / (n - 1);
-  double Delta;
+  double Delta, R;
   if (i < n / 2) {
     // x = 1/2 - sqrt(-log(1 - e^2/mu)/50): eta = 1 - e^2/mu = exp(-50 (1/2 - x)^2)
     double a = 0.5 - x;
     double eta = exp(-50.0 * a * a);
+    double e = sqrt(-kMu * expm1(-50.0 * a * a));
     Apsis ap = apsis_of_eta(eta);
     double w0 = sqrt(ap.ua) * (1.0 - y);  // y = 1 - sqrt(1 - u/u_a)
     double u = ap.ua - w0 * w0;
-    double phi = phi_scatter(ap, w0);
+    double phi = scatter_integral<false>(ap, e, w0);
     double udot = w0 * sqrt(qw(ap, w0));
     Delta = phi - atan2(u, udot);
+    R = scatter_integral<true>(ap, e, w0);
   } else {
     // x = 1/2 + sqrt(-log(1 - mu/e^2)/50): 1 - mu/e^2 = exp(-50 (x - 1/2)^2)
     double a = x - 0.5;
@@ -195,12 +216,16 @@ __global__ void precompute_D_kernel(int n, double *D64, T *Ds) {
     double z = y * (r23 + r13) - r23;
     double v = z >= 0.0 ? z * z : -z * z;  // u - 2/3
     double u = 2.0 / 3.0 + v;
-    double phi = phi_plunge(se, asinh(-2.0 / 3.0 / se), asinh(v / se));
+    double ta = asinh(-2.0 / 3.0 / se), tb = asinh(v / se);
+    double phi = plunge_integral<false>(se, 0.0, ta, tb);
     double udot = sqrt(em + v * v * (v + 1.0));
     Delta = phi - atan2(u, udot);
+    R = plunge_integral<true>(se, sqrt(e2), ta, tb);
   }
   D64[(size_t)j * n + i] = Delta;
   Ds[(size_t)j * n + i] = to_storage<T>(Delta);
+  DT64[(size_t)j * n + i] = R;
+  DTs[(size_t)j * n + i] = (float)R;
 }
 
 // Warp-cooperative forms of the quadratures above: the 32 lanes of a warp
@@ -211,59 +236,73 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ double warp_quad_w(const Apsis &a, double w0, double w1, int panels, int lane) {
+template <bool TIME>
+__device__ double warp_quad_w(const Apsis &a, double e, double w0, double w1, int panels, int lane) {
   double h = (w1 - w0) / panels, s = 0.0;
   for (int idx = lane; idx < panels * kGL; idx += 32) {
     int p = idx / kGL, k = idx % kGL;
     double c = w0 + (p + 0.5) * h, r = 0.5 * h;
-    s += cGLw[k] * r * 2.0 * rsqrt(qw(a, c + r * cGLx[k]));
+    double w = c + r * cGLx[k], q = qw(a, w), rq = rsqrt(q);
+    double f = 2.0 * rq;
+    if (TIME) f /= e + w * q * rq;
+    s += cGLw[k] * r * f;
   }
   return warp_sum(s);
 }
 
-__device__ double warp_quad_t_scatter(const Apsis &a, double c, double t0, double t1, int panels,
+template <bool TIME>
+__device__ double warp_quad_t_scatter(const Apsis &a, double e, double c, double t0, double t1, int panels,
                                       int lane) {
   double h = (t1 - t0) / panels, s = 0.0;
   for (int idx = lane; idx < panels * kGL; idx += 32) {
     int p = idx / kGL, k = idx % kGL;
     double m = t0 + (p + 0.5) * h, r = 0.5 * h;
-    double sh = sinh(m + r * cGLx[k]);
-    s += cGLw[k] * r * 2.0 * c * sqrt(1.0 + sh * sh) * rsqrt(qw(a, c * sh));
+    double sh = sinh(m + r * cGLx[k]), w = c * sh, q = qw(a, w), rq = rsqrt(q);
+    double f = 2.0 * c * sqrt(1.0 + sh * sh) * rq;
+    if (TIME) f /= e + w * q * rq;
+    s += cGLw[k] * r * f;
   }
   return warp_sum(s);
 }
 
-__device__ double warp_phi_scatter(const Apsis &a, double w0, int lane) {
+template <bool TIME>
+__device__ double warp_scatter_integral(const Apsis &a, double e, double w0, int lane) {
   double w1 = sqrt(a.ua);
   if (a.ua > 0.6) {
     double c = sqrt(a.A / a.B);
     double wm = fmax(w0, fmin(w1, 0.35));
-    return warp_quad_t_scatter(a, c, asinh(w0 / c), asinh(wm / c), 6, lane) + warp_quad_w(a, wm, w1, 4, lane);
+    return warp_quad_t_scatter<TIME>(a, e, c, asinh(w0 / c), asinh(wm / c), 6, lane) +
+           warp_quad_w<TIME>(a, e, wm, w1, 4, lane);
   }
-  return warp_quad_w(a, w0, w1, 4, lane);
+  return warp_quad_w<TIME>(a, e, w0, w1, 4, lane);
 }
 
-__device__ double warp_phi_plunge(double se, double ta, double tb, int lane) {
+template <bool TIME>
+__device__ double warp_plunge_integral(double se, double e, double ta, double tb, int lane) {
   const int panels = 6;
   double h = (tb - ta) / panels, s = 0.0;
   for (int idx = lane; idx < panels * kGL; idx += 32) {
     int p = idx / kGL, k = idx % kGL;
     double t = ta + (p + 0.5) * h + 0.5 * h * cGLx[k];
-    double th = tanh(t);
-    s += cGLw[k] * 0.5 * h * rsqrt(1.0 + se * sinh(t) * th * th);
+    double th = tanh(t), g = 1.0 + se * sinh(t) * th * th, rg = rsqrt(g);
+    double f = rg;
+    if (TIME) f /= e + se * cosh(t) * g * rg;
+    s += cGLw[k] * 0.5 * h * f;
   }
   return warp_sum(s);
 }
 
 // U(e,phi) per texel, one warp per texel: x = 1/(1 + 6 e^2),
-// y = (phi/3)(1 + 6 e^3)/(1 + e^2).
+// y = (phi/3)(1 + 6 e^3)/(1 + e^2).  UT gets the regularised time at the
+// same point; past the apsis it follows from the time symmetry of the ray
+// about its apsis, t(phi) = 2 t_a - t(2 phi_a - phi).
 template <typename T>
-__global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
+__global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us, double *UT64, float *UTs) {
   int lane = threadIdx.x & 31;
   int texel = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (texel >= ne * nphi) return;  // whole warps leave together
   int i = texel % ne, j = texel / ne;
-  double u;
+  double u, R = 0.0;  // R = 0 where there is no ray or it was captured
   if (i == 0) {
     u = j == 0 ? 0.0 : 1.0;  // e -> infinity: radial ray, captured at once
   } else {
@@ -275,11 +314,12 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
       u = 0.0;
     } else if (e2 < kMu) {
       Apsis ap = apsis_of_eta(1.0 - e2 / kMu);
-      double phia = warp_phi_scatter(ap, 0.0, lane);
-      if (phi > phia) phi = 2.0 * phia - phi;  // past the apsis: reflection
+      double phia = warp_scatter_integral<false>(ap, e, 0.0, lane);
+      bool past = phi > phia;
+      if (past) phi = 2.0 * phia - phi;  // past the apsis: reflection
       double lo = 0.0, hi = sqrt(ap.ua), w = 0.5 * (lo + hi);
       for (int it = 0; it < 80; ++it) {
-        double F = warp_phi_scatter(ap, w, lane) - phi;  // decreasing in w
+        double F = warp_scatter_integral<false>(ap, e, w, lane) - phi;  // decreasing in w
         if (F > 0.0) lo = w; else hi = w;
         double dF = -2.0 * rsqrt(qw(ap, w));
         double wn = w - F / dF;
@@ -288,15 +328,25 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
         w = wn;
       }
       u = ap.ua - w * w;
+      R = warp_scatter_integral<true>(ap, e, w, lane);
+      if (past) {
+        if (u > 0.0) {
+          double Ra = warp_scatter_integral<true>(ap, e, 0.0, lane);
+          double l = 2.0 * log(u / (1.0 - u)), la = 2.0 * log(ap.ua / (1.0 - ap.ua));
+          R = 2.0 * Ra - 2.0 / ap.ua + la - R + 2.0 / u - l;
+        } else {
+          R = 0.0;  // back at infinity: no texel of the mapping gets here
+        }
+      }
     } else {
       double se = sqrt(e2 - kMu);
       double ta = asinh(-2.0 / 3.0 / se), tb = asinh(1.0 / 3.0 / se);
-      if (phi >= warp_phi_plunge(se, ta, tb, lane)) {
+      if (phi >= warp_plunge_integral<false>(se, e, ta, tb, lane)) {
         u = 1.0;  // reached the horizon before phi (reading C7)
       } else {
         double lo = ta, hi = tb, t = 0.5 * (lo + hi);
         for (int it = 0; it < 80; ++it) {
-          double F = warp_phi_plunge(se, ta, t, lane) - phi;  // increasing in t
+          double F = warp_plunge_integral<false>(se, e, ta, t, lane) - phi;  // increasing in t
           if (F < 0.0) lo = t; else hi = t;
           double th = tanh(t);
           double dF = rsqrt(1.0 + se * sinh(t) * th * th);
@@ -306,12 +356,15 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us) {
           t = tn;
         }
         u = 2.0 / 3.0 + se * sinh(t);
+        R = warp_plunge_integral<true>(se, e, ta, t, lane);
       }
     }
   }
   if (lane == 0) {
     U64[(size_t)j * ne + i] = u;
     Us[(size_t)j * ne + i] = to_storage<T>(u);
+    UT64[(size_t)j * ne + i] = R;
+    UTs[(size_t)j * ne + i] = (float)R;
   }
 }
 
@@ -427,6 +480,8 @@ extern "C" bh_status bh_create(int device, size_t budget, bh_ctx **out) {
   cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMalloc((void **)&c->status_dev, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(c->status_dev, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->sched_dev, sizeof(unsigned) * 2 * kSchedRing);
+  if (e == cudaSuccess) e = cudaMemset(c->sched_dev, 0, sizeof(unsigned) * 2 * kSchedRing);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     bh_destroy(c);
@@ -463,6 +518,7 @@ extern "C" void bh_destroy(bh_ctx *c) {
   cudaDeviceSynchronize();
   c->graph.reset();
   if (c->status_dev) cudaFree(c->status_dev);
+  if (c->sched_dev) cudaFree(c->sched_dev);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->cam_host) cudaFreeHost(c->cam_host);
   if (c->cam_dev) cudaFree(c->cam_dev);
@@ -507,6 +563,10 @@ static bh_status tables_alloc(bh_ctx *ctx, const bh_table_desc *desc, cudaStream
   if (e == cudaSuccess) e = cudaMalloc((void **)&t->U64, nu * 8);
   if (e == cudaSuccess) e = cudaMalloc(&t->D, nd * es);
   if (e == cudaSuccess) e = cudaMalloc(&t->U, ((nu * es + 15) / 16) * 16);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&t->DT64, nd * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&t->UT64, nu * 8);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&t->DT, nd * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&t->UT, nu * 4);
   if (e == cudaSuccess) e = cudaMalloc((void **)&t->C, sizeof(float4) * kCnx * kCny * kCnd);
   if (e == cudaSuccess) e = cudaMalloc((void **)&t->disc, sizeof(float4) * kDiscN);
   if (e != cudaSuccess) {
@@ -532,11 +592,13 @@ extern "C" bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc
   dim3 gd((n + 127) / 128, n);
   unsigned gu = (unsigned)((desc->u_ne * desc->u_nphi + 3) / 4);  // 4 warps (texels) per block
   if (desc->storage == BH_F32) {
-    precompute_D_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D);
-    precompute_U_kernel<float><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (float *)t->U);
+    precompute_D_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D, t->DT64, t->DT);
+    precompute_U_kernel<float><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (float *)t->U, t->UT64,
+                                                 t->UT);
   } else {
-    precompute_D_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D);
-    precompute_U_kernel<__half><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (__half *)t->U);
+    precompute_D_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D, t->DT64, t->DT);
+    precompute_U_kernel<__half><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (__half *)t->U, t->UT64,
+                                                  t->UT);
   }
   count_launch(ctx, 2);
   cudaError_t e = cudaGetLastError();
@@ -560,6 +622,11 @@ extern "C" bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, co
   size_t nd = (size_t)desc->d_n * desc->d_n, nu = (size_t)desc->u_ne * desc->u_nphi;
   cudaError_t e = cudaMemcpyAsync(t->D64, Dh, nd * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(t->U64, Uh, nu * 8, cudaMemcpyHostToDevice, s);
+  // no time channel until bh_tables_upload_time: all-ones bytes read as NaN
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->DT64, 0xff, nd * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->UT64, 0xff, nu * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->DT, 0xff, nd * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->UT, 0xff, nu * 4, s);
   if (e == cudaSuccess) {
     if (desc->storage == BH_F32) {
       convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (float *)t->D, nd);
@@ -590,6 +657,31 @@ extern "C" bh_status bh_tables_copy_out(const bh_tables *t, double *Dh, double *
   return BH_OK;
 }
 
+extern "C" bh_status bh_tables_upload_time(bh_tables *t, const double *DTh, const double *UTh, void *stream) {
+  if (!t || !DTh || !UTh) { set_error("bh_tables_upload_time: NULL argument"); return BH_ERR_INVALID_ARG; }
+  BH_CUDA(cudaSetDevice(t->ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t nd = (size_t)t->desc.d_n * t->desc.d_n, nu = (size_t)t->desc.u_ne * t->desc.u_nphi;
+  BH_CUDA(cudaMemcpyAsync(t->DT64, DTh, nd * 8, cudaMemcpyHostToDevice, s));
+  BH_CUDA(cudaMemcpyAsync(t->UT64, UTh, nu * 8, cudaMemcpyHostToDevice, s));
+  convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->DT64, t->DT, nd);
+  convert_kernel<float><<<(nu + 255) / 256, 256, 0, s>>>(t->UT64, t->UT, nu);
+  count_launch(t->ctx, 2);
+  BH_CUDA(cudaGetLastError());
+  BH_CUDA(cudaStreamSynchronize(s));
+  return BH_OK;
+}
+
+extern "C" bh_status bh_tables_copy_time(const bh_tables *t, double *DTh, double *UTh) {
+  if (!t) { set_error("bh_tables_copy_time: NULL tables"); return BH_ERR_INVALID_ARG; }
+  BH_CUDA(cudaSetDevice(t->ctx->device));
+  BH_CUDA(cudaDeviceSynchronize());
+  if (DTh) BH_CUDA(cudaMemcpy(DTh, t->DT64, sizeof(double) * t->desc.d_n * t->desc.d_n, cudaMemcpyDeviceToHost));
+  if (UTh)
+    BH_CUDA(cudaMemcpy(UTh, t->UT64, sizeof(double) * t->desc.u_ne * t->desc.u_nphi, cudaMemcpyDeviceToHost));
+  return BH_OK;
+}
+
 extern "C" bh_status bh_tables_copy_colour(const bh_tables *t, float *Ch, float *dh) {
   if (!t) { set_error("bh_tables_copy_colour: NULL tables"); return BH_ERR_INVALID_ARG; }
   BH_CUDA(cudaSetDevice(t->ctx->device));
@@ -607,6 +699,10 @@ extern "C" void bh_tables_free(bh_tables *t) {
   cudaFree(t->U64);
   cudaFree(t->D);
   cudaFree(t->U);
+  cudaFree(t->DT64);
+  cudaFree(t->UT64);
+  cudaFree(t->DT);
+  cudaFree(t->UT);
   cudaFree(t->C);
   cudaFree(t->disc);
   delete t;

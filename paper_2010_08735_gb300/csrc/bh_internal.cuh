@@ -64,9 +64,14 @@ struct BatchGraph {
 
 struct RenderTuning {
   int warps_per_block = 8;   // block = warps * 32 threads
-  int block_w = 32;          // block tile width in pixels (multiple of 8)
-  int blocks_per_sm = 8;     // persistent grid = SMs * blocks_per_sm
+  int fetch = 2;             // 8 x 4 pixel warp tiles a warp takes per fetch
+  int blocks_per_sm = 4;     // persistent grid = SMs * blocks_per_sm
 };
+
+// Tile-scheduler counters: every render launch takes the next pair of a ring
+// (re-armed to zero by the launch's last warp), so launches in flight at once
+// on different streams need distinct pairs: at most kSchedRing of them.
+constexpr int kSchedRing = 1024;
 
 }  // namespace bh
 
@@ -76,6 +81,8 @@ struct bh_ctx {
   size_t budget = 0;
   cudaStream_t aux = nullptr;
   unsigned *status_dev = nullptr;     // kernel status word
+  unsigned *sched_dev = nullptr;      // kSchedRing pairs of tile-scheduler counters
+  std::atomic<unsigned> sched_next{0};
   std::atomic<long long> launches{0};
   // render staging: per-camera constants for batched launches
   void *cam_host = nullptr;           // pinned
@@ -102,6 +109,8 @@ struct bh_tables {
   bh_table_desc desc{};
   double *D64 = nullptr, *U64 = nullptr;  // FP64 values
   void *D = nullptr, *U = nullptr;        // storage copies read by the renderer
+  double *DT64 = nullptr, *UT64 = nullptr;  // regularised-time channels of D and U (FP64)
+  float *DT = nullptr, *UT = nullptr;       // their FP32 copies (read by the debug render)
   float4 *C = nullptr;                    // colour shift table [k][j][i] (XYZ, pad)
   float4 *disc = nullptr;                 // ln Y, X/Y, Z/Y of black bodies, log2 T in [8, 20]
 };

@@ -41,13 +41,15 @@ struct CamConst {
 struct RenderParams {
   CamConst cam0;            // single-camera launches
   const CamConst *cams;     // batched launches (nullptr: cam0)
-  int ncams, total_tiles;
+  int ncams, total_tiles;   // tiles are 8 x 4 pixel warp tiles, row-major per camera
   const int *total_tiles_dev;  // if set, the tile count computed on the device
-  int bw, bh, warps_x;      // block tile (pixels) and warps across
+  unsigned *sched;          // {next fetch, retired warps}: zero before and after every launch
+  int fetch;                // warp tiles taken per fetch
   const void *D;
   int d_n;
   const void *U;
   int u_ne, u_nphi, u_bytes;
+  const float *DTt, *UTt;   // regularised-time channels of D and U (debug render only)
   const float4 *C;
   const float4 *disc;
   const uint2 *cube;
@@ -72,6 +74,7 @@ __device__ __forceinline__ float sm_tab(const float *p, int i) { return p[i]; }
 __device__ __forceinline__ float sm_tab(const __half *p, int i) { return __half2float(p[i]); }
 
 constexpr float kMuF = 4.0f / 27.0f;
+constexpr int kDbgFloats = 20;  // debug values per pixel (five float4)
 constexpr float kPiF = 3.14159265358979f;
 
 // Bilinear D lookup at Appendix A coordinates; x clamped to its branch (C2).
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         : "memory");
   }
   __syncthreads();
+  bool table_ok;
   {
     // bounded waits: give up after a limit of global time
     auto bounded_wait = [](unsigned bar, unsigned long long limit_ns) -> bool {
@@ -159,16 +163,13 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     if (!ok) bounded_wait(mb, P.wait_ns);  // let copies still in flight land before leaving
     // fault injection (bh_inject_fault): a barrier nothing arrives at
     if (ok && P.inject_wait) ok = bounded_wait(mb_never, P.inject_wait_ns);
-    if (!ok) {
-      if (threadIdx.x == 0) atomicOr(P.status, kStatusMbarTimeout);
-      return;
-    }
+    if (!ok && threadIdx.x == 0) atomicOr(P.status, kStatusMbarTimeout);
+    table_ok = ok;
   }
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int lx = ((lane >> 2) & 3) * 2 + (lane & 1);
   const int ly = ((lane >> 4) & 1) * 2 + ((lane >> 1) & 1);
-  const int wx = warp % P.warps_x, wy = warp / P.warps_x;
   const int dn = P.d_n;
   const DT *D = reinterpret_cast<const DT *>(P.D);
   const int n_half = dn / 2;
@@ -183,8 +184,20 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     y_peak = expf(fmaf(t, s_disc[k1].x - s_disc[k0].x, s_disc[k0].x));
   }
 
+  // Dynamic schedule: each warp takes the next P.fetch warp tiles from a
+  // global counter until none are left, so no warp idles while work remains.
   const int total_tiles = P.total_tiles_dev ? *P.total_tiles_dev : P.total_tiles;
-  for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+  int tile = 0, tile_end = 0;
+  for (;;) {
+    if (tile == tile_end) {
+      unsigned g = 0;
+      if (lane == 0 && table_ok) g = atomicAdd(P.sched, 1u);
+      g = __shfl_sync(0xffffffffu, g, 0);
+      long long first = (long long)g * P.fetch;
+      if (!table_ok || first >= total_tiles) break;
+      tile = (int)first;
+      tile_end = (int)min(first + P.fetch, (long long)total_tiles);
+    }
     // ---- which camera and which tile of it
     const CamConst *cp = &P.cam0;
     if (P.cams) {
@@ -197,8 +210,9 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     }
     const CamConst &C = *cp;
     int t = tile - C.tile0;
+    ++tile;
     int ty = t / C.tiles_x, tx = t - ty * C.tiles_x;
-    int px = tx * P.bw + wx * 8 + lx, py = ty * P.bh + wy * 4 + ly;
+    int px = tx * 8 + lx, py = ty * 4 + ly;
 
     // ---- beam initialisation (Eq. d, Eq. raybasis, Eq. alpha)
     float qw = (px + 0.5f) - C.half_w, qh = C.half_h - (py + 0.5f), qd = -C.f;
@@ -240,7 +254,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       float ic = 1.f / cn;
       z0 = c0 * ic; z1 = c1 * ic; z2 = c2 * ic;
     }
-    float y0 = z1 * x2 - z2 * x1, y1 = z2 * x0 - z0 * x2, y2 = z0 * x1 - z1 * x0;
+    // e_y' = e_z' ^ e_x' (its z component is not needed below)
+    float y0 = z1 * x2 - z2 * x1, y1 = z2 * x0 - z0 * x2;
     bool alpha_ok = false;
     float alpha = 0.f;
     {
@@ -264,6 +279,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     bool captured = false;
     int nh = 0;
     float hu0 = 0.f, hu1 = 0.f;
+    float th0 = 0.f, th1 = 0.f;  // retarded-time delays of the hits (debug render)
     float delta_p = 0.f, turn = 0.f;  // delta' = delta + turn
     if (em < 0.f && u > 2.f / 3.f) {
       captured = true;
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       float xd = d_x(e2, em);
       float fx = xd * (dn - 1);
       int xlo = em < 0.f ? 0 : n_half, xhi = em < 0.f ? n_half - 1 : dn - 1;
-      float ua = 0.f, Dl, Da = 0.f, phia = INFINITY;
+      float ua = 0.f, Dl, Da = 0.f, phia = INFINITY, yv;
       if (em < 0.f) {
         float eta = -em / kMuF;
         float sa = asinf(sqrtf(fminf(eta, 1.f)));
@@ -282,14 +298,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         // no cancellation when the camera is near the apsis (du/dphi -> 0)
         float g = ua + u - ua * ua - ua * u - u * u;
         float om = g > 0.f ? udot * udot / (ua * g) : 1.f - u / ua;
-        float yv = 1.f - sqrtf(fmaxf(om, 0.f));
+        yv = 1.f - sqrtf(fmaxf(om, 0.f));
         Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
         Da = d_bilinear(D, dn, fx, (float)(dn - 1), xlo, xhi);
         phia = Da + 0.5f * kPiF;
       } else {
         const float r23 = 0.81649658f, r13 = 0.57735027f;
         float sq = sqrtf(fabsf(um));
-        float yv = (r23 + (um >= 0.f ? sq : -sq)) / (r23 + r13);
+        yv = (r23 + (um >= 0.f ? sq : -sq)) / (r23 + r13);
         Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
       }
       if (alpha_ok && P.disc_on) {
@@ -308,19 +324,39 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
           return fmaf(ty2, hi - lo, lo);
         };
+        // retarded times (debug only): t = R - 1/u + ln(u/(1-u)) of the
+        // camera point and of the apsis, from the time channel of D
+        float tcam = 0.f, tapsis = 0.f;
+        auto t_of_R = [](float R, float uu) { return R - 1.f / uu + logf(uu / (1.f - uu)); };
+        auto ulookT = [&](float ph) {
+          float fy = fminf(fmaxf(ph * yk * (P.u_nphi - 1), 0.f), (float)(P.u_nphi - 1));
+          int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
+          float ty2 = fy - j0;
+          float a = __ldg(P.UTt + j0 * P.u_ne + ui0), b = __ldg(P.UTt + j0 * P.u_ne + ui1);
+          float c = __ldg(P.UTt + j1 * P.u_ne + ui0), d = __ldg(P.UTt + j1 * P.u_ne + ui1);
+          float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
+          return fmaf(ty2, hi - lo, lo);
+        };
+        if (DEBUG) {
+          tcam = t_of_R(d_bilinear(P.DTt, dn, fx, yv * (dn - 1), xlo, xhi), u);
+          if (em < 0.f) tapsis = t_of_R(d_bilinear(P.DTt, dn, fx, (float)(dn - 1), xlo, xhi), ua);
+        }
         float phi = Dl + (s == 1 ? kPiF - delta : delta) + s * alpha;
         float phi0 = phi - kPiF * floorf(phi / kPiF);
         float u0 = ulook(phi0);
         if (phi0 < phia && P.u_oc <= u0 && u0 <= P.u_ic && ((s == 1 && u0 > u) || (s == -1 && u0 < u))) {
           hu0 = u0;
           nh = 1;
+          if (DEBUG) th0 = (float)s * (t_of_R(ulookT(phi0), u0) - tcam);
         }
         if (em < 0.f && s == 1) {
           phi = 2.f * phia - phi;
           float phi1 = phi - kPiF * floorf(phi / kPiF);
           float u1 = ulook(phi1);
           if (phi1 < phia && P.u_oc <= u1 && u1 <= P.u_ic) {
-            if (nh == 0) hu0 = u1; else hu1 = u1;
+            float tk = 0.f;
+            if (DEBUG) tk = 2.f * tapsis - tcam - t_of_R(ulookT(phi1), u1);
+            if (nh == 0) { hu0 = u1; th0 = tk; } else { hu1 = u1; th1 = tk; }
             ++nh;
           }
         }
@@ -478,11 +514,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
             SZ = fmaf(wt, Z, SZ);
           };
           const bool straddle = b0 + nrow > 32 && w0i + 1 < wpr;
-          for (int jj = j0; jj <= j1; ++jj) {
+          auto row_bits = [&](const int jj) {
             const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
             unsigned long long win = __ldg(mrow);
             if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
-            unsigned bits = (unsigned)(win >> b0) & rowbits;
+            return (unsigned)(win >> b0) & rowbits;
+          };
+          for (int jj = j0; jj <= j1; ++jj) {
+            unsigned bits = row_bits(jj);
             if (nrow > 0) visited += nrow;
             while (bits) {
               const int k = __ffs(bits) - 1;
@@ -530,13 +569,24 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       long long o = (long long)py * C.width + px;
       C.out[o] = make_float4(R_, G_, B_, 1.f);
       if (DEBUG) {
-        float *g = C.dbg + o * 16;
+        float *g = C.dbg + o * kDbgFloats;
         float4 *g4 = reinterpret_cast<float4 *>(g);
         g4[0] = make_float4(e2, delta, captured ? INFINITY : delta_p, (float)nh);
         g4[1] = make_float4(hu0, hu1, (float)(anycap ? -1 : level), (float)(anycap ? -1 : face));
         g4[2] = make_float4(omega, dstar, SX, SY);
         g4[3] = make_float4(SZ, dop0, dop1, (float)visited);
+        g4[4] = make_float4(th0, th1, 0.f, 0.f);
       }
+    }
+  }
+  // Retire the warp; the last warp of the grid re-arms the counters for the
+  // next launch that uses them (every warp has taken its final fetch by then).
+  if (lane == 0) {
+    __threadfence();
+    unsigned nw = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(P.sched + 1, 1u) == nw - 1u) {
+      atomicExch(P.sched, 0u);
+      atomicExch(P.sched + 1, 0u);
     }
   }
 }
@@ -676,6 +726,8 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
   P.u_nphi = t->desc.u_nphi;
   size_t es = t->desc.storage == BH_F32 ? 4 : 2;
   P.u_bytes = (int)(((size_t)P.u_ne * P.u_nphi * es + 15) / 16 * 16);
+  P.DTt = t->DT;
+  P.UTt = t->UT;
   P.C = t->C;
   P.disc = t->disc;
   if (cube) {
@@ -706,16 +758,26 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
     P.inject_wait = 1;
     ctx->inject_table_wait = 0;
   }
-  P.bw = ctx->tuning.block_w;
-  P.warps_x = P.bw / 8;
-  P.bh = 4 * (ctx->tuning.warps_per_block / P.warps_x);
+  P.fetch = ctx->tuning.fetch;
+  P.sched = ctx->sched_dev + 2 * (ctx->sched_next.fetch_add(1, std::memory_order_relaxed) % kSchedRing);
   return BH_OK;
+}
+
+// Warp tiles (8 x 4 pixels) of a w x h image.
+static inline int tiles_across(int w) { return (w + 7) / 8; }
+static inline int warp_tiles(int w, int h) { return tiles_across(w) * ((h + 3) / 4); }
+
+// Persistent grid: enough blocks to fill the GPU, no more than the work needs.
+static int render_grid(const bh_ctx *ctx, long long tiles) {
+  long long per_block = (long long)ctx->tuning.warps_per_block * ctx->tuning.fetch;
+  long long need = (tiles + per_block - 1) / per_block;
+  return (int)std::min<long long>(need, (long long)ctx->sm_count * ctx->tuning.blocks_per_sm);
 }
 
 static bh_status launch(bh_ctx *ctx, const bh_tables *t, RenderParams &P, bool debug, cudaStream_t s) {
   int threads = 32 * ctx->tuning.warps_per_block;
   size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
-  int grid = std::min(P.total_tiles, ctx->sm_count * ctx->tuning.blocks_per_sm);
+  int grid = render_grid(ctx, P.total_tiles);
   if (grid < 1) return BH_OK;
   bool half = t->desc.storage == BH_F16;
   if (!half && !debug) render_kernel<float, false><<<grid, threads, smem, s>>>(P);
@@ -740,13 +802,13 @@ static bh_status render_one(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   RenderParams P;
   fill_params(ctx, t, cube, disc, sh, P);
   camera_constants(cam, &P.cam0);
-  P.cam0.tiles_x = (cam->width + P.bw - 1) / P.bw;
+  P.cam0.tiles_x = tiles_across(cam->width);
   P.cam0.tile0 = 0;
   P.cam0.out = reinterpret_cast<float4 *>(out);
   P.cam0.dbg = dbg;
   P.cams = nullptr;
   P.ncams = 1;
-  P.total_tiles = P.cam0.tiles_x * ((cam->height + P.bh - 1) / P.bh);
+  P.total_tiles = warp_tiles(cam->width, cam->height);
   return launch(ctx, t, P, dbg != nullptr, s);
 }
 
@@ -779,18 +841,18 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   int tiles = 0;
   for (int k = 0; k < n; ++k) {
     camera_constants(&cams[k], &h[k]);
-    h[k].tiles_x = (cams[k].width + P.bw - 1) / P.bw;
+    h[k].tiles_x = tiles_across(cams[k].width);
     h[k].tile0 = tiles;
     h[k].out = reinterpret_cast<float4 *>(outs[k]);
     h[k].dbg = nullptr;
-    tiles += h[k].tiles_x * ((cams[k].height + P.bh - 1) / P.bh);
+    tiles += warp_tiles(cams[k].width, cams[k].height);
   }
   P.cams = static_cast<const CamConst *>(cam_dev);
   P.ncams = n;
   P.total_tiles = tiles;
   int threads = 32 * ctx->tuning.warps_per_block;
   size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
-  int grid = std::min(P.total_tiles, ctx->sm_count * ctx->tuning.blocks_per_sm);
+  int grid = render_grid(ctx, P.total_tiles);
   if (grid < 1) return BH_OK;
   const void *func = kernel_ptr(t->desc.storage == BH_F16, false);
   void *args[] = {&P};
@@ -893,13 +955,13 @@ __global__ void orbit_advance_kernel(bh_orbit *orbits, int n, double dtau, int s
 // Camera constants of every orbit (one block), then the tile offsets (one
 // thread, in camera order) -- the same layout bh_render_batch stages from the
 // host.
-__global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *const *outs, int bw, int bh,
-                                      CamConst *cams, int *total_tiles) {
+__global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *const *outs, CamConst *cams,
+                                      int *total_tiles) {
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     bh_camera c;
     orbit_to_camera(&orbits[k], &c);
     camera_constants(&c, &cams[k]);
-    cams[k].tiles_x = (c.width + bw - 1) / bw;
+    cams[k].tiles_x = (c.width + 7) / 8;  // 8 x 4 pixel warp tiles
     cams[k].out = reinterpret_cast<float4 *>(outs[k]);
     cams[k].dbg = nullptr;
   }
@@ -908,7 +970,7 @@ __global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *cons
     int tiles = 0;
     for (int j = 0; j < n; ++j) {
       cams[j].tile0 = tiles;
-      tiles += cams[j].tiles_x * ((orbits[j].height + bh - 1) / bh);
+      tiles += cams[j].tiles_x * ((orbits[j].height + 3) / 4);
     }
     *total_tiles = tiles;
   }
@@ -992,10 +1054,9 @@ extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh
   bh_status st = validate_batch(n, cams, disc, outs);
   if (st) return st;
   BH_CUDA(cudaSetDevice(ctx->device));
-  // candidates: warps per block, block tile width, resident blocks per SM
-  static const RenderTuning cand[] = {{8, 32, 4}, {8, 16, 4}, {8, 64, 4},  {4, 32, 8},
-                                      {4, 16, 8}, {8, 32, 2}, {8, 32, 8},  {8, 8, 4},
-                                      {8, 32, 16}, {8, 16, 8}, {8, 16, 16}, {4, 32, 16}};
+  // candidates: warps per block, warp tiles per fetch, resident blocks per SM
+  static const RenderTuning cand[] = {{8, 1, 4}, {8, 2, 4}, {8, 4, 4}, {8, 8, 4},
+                                      {4, 1, 8}, {4, 2, 8}, {4, 4, 8}, {8, 16, 4}};
   const int nc = sizeof(cand) / sizeof(cand[0]);
   cudaStream_t s;
   BH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -1116,7 +1177,7 @@ extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_
   RenderParams P;
   fill_params(ctx, t, cube, disc, sh, P);
   CamConst *cams = static_cast<CamConst *>(ctx->orb_cams_dev);
-  orbit_camconst_kernel<<<1, 256, 0, s>>>(orbits_device, n, pd, P.bw, P.bh, cams, total_dev);
+  orbit_camconst_kernel<<<1, 256, 0, s>>>(orbits_device, n, pd, cams, total_dev);
   count_launch(ctx);
   P.cams = cams;
   P.ncams = n;

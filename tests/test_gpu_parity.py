@@ -35,8 +35,14 @@ def ctx():
 
 
 @pytest.fixture(scope="module")
-def orc_tables(orc):
-    return orc.tables_exact(512, 64, 32, 1e-3)
+def orc_tables_t(orc):
+    """D, U and their regularised-time channels DT, UT."""
+    return orc.tables_exact_t(512, 64, 32, 1e-3)
+
+
+@pytest.fixture(scope="module")
+def orc_tables(orc_tables_t):
+    return orc_tables_t[:2]
 
 
 @pytest.fixture(scope="module")
@@ -72,16 +78,43 @@ def test_tables_match_oracle(gpu_tables, orc_tables):
     assert errU.max() <= TABLE_REL, np.unravel_index(errU.argmax(), errU.shape)
 
 
+def test_time_tables_match_oracle(gpu_tables, orc_tables_t):
+    """Regularised-time channels (Algorithm 1 stores t beside Delta and u)."""
+    DTg, UTg = bh.bh_tables_copy_time(gpu_tables, 512, 64, 32)
+    DTo, UTo = orc_tables_t[2:]
+    errD = np.abs(DTg - DTo) / (np.abs(DTo) + 1e-3)
+    assert errD.max() <= TABLE_REL, np.unravel_index(errD.argmax(), errD.shape)
+    errU = np.abs(UTg - UTo) / (np.abs(UTo) + 1e-3)
+    assert errU.max() <= TABLE_REL, np.unravel_index(errU.argmax(), errU.shape)
+
+
 @pytest.mark.parametrize("dn,une,unphi", [(66, 10, 6), (128, 16, 16), (4, 2, 2)])
 def test_tables_small_and_ragged(ctx, orc, dn, une, unphi):
     t = bh.bh_precompute_tables(ctx, dn, une, unphi, bh.BH_F16)
     try:
         Dg, Ug = bh.bh_tables_copy_out(t, dn, une, unphi)
+        DTg, UTg = bh.bh_tables_copy_time(t, dn, une, unphi)
     finally:
         bh.bh_tables_free(t)
-    Do, Uo = orc.tables_exact(dn, une, unphi, 1e-3)
+    Do, Uo, DTo, UTo = orc.tables_exact_t(dn, une, unphi, 1e-3)
     assert (np.abs(Dg - Do) / (np.abs(Do) + 1e-3)).max() <= TABLE_REL
     assert (np.abs(Ug - Uo) / (np.abs(Uo) + 1e-6)).max() <= TABLE_REL
+    assert (np.abs(DTg - DTo) / (np.abs(DTo) + 1e-3)).max() <= TABLE_REL
+    assert (np.abs(UTg - UTo) / (np.abs(UTo) + 1e-3)).max() <= TABLE_REL
+
+
+def test_uploaded_tables_time_channel(ctx, orc_tables_t):
+    """Uploaded tables carry NaN time channels until bh_tables_upload_time."""
+    D, U, DT, UT = orc_tables_t
+    t = bh.bh_tables_upload(ctx, D, U, bh.BH_F16)
+    try:
+        DTg, UTg = bh.bh_tables_copy_time(t, 512, 64, 32)
+        assert np.isnan(DTg).all() and np.isnan(UTg).all()
+        bh.bh_tables_upload_time(t, DT, UT)
+        DTg, UTg = bh.bh_tables_copy_time(t, 512, 64, 32)
+        assert np.array_equal(DTg, DT) and np.array_equal(UTg, UT)
+    finally:
+        bh.bh_tables_free(t)
 
 
 def test_colour_tables_match_oracle(gpu_tables, orc_colour):
@@ -146,7 +179,7 @@ def gpu_render(ctx, tables, cube, cam, disc, debug=True, exposure_stars=EXPOSURE
     out = torch.zeros((H, W, 4), device="cuda")
     sh = bh.make_shading(1.0, exposure_stars)
     if debug:
-        dbg = torch.zeros((H, W, 16), device="cuda")
+        dbg = torch.zeros((H, W, bh.NDBG), device="cuda")
         bh.bh_render_debug(ctx, tables, cube, cam, disc, sh, out, dbg)
         torch.cuda.synchronize()
         return out.cpu().numpy(), dbg.cpu().numpy()
@@ -239,6 +272,52 @@ def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_sce
     check_rgb(og, oo, od, mask, wk["camera"])
 
 
+DELAY_CAMS = [
+    (synth.WORKLOADS["static_256"]["camera"], synth.WORKLOADS["static_256"]["disc"]),
+    (synth.camera(25.0, 60.0, phi_deg=40.0, v=(0.2, -0.3, 0.1), width=97, height=61), synth.disc(3.0, 20.0)),
+    (synth.camera(3.2, 89.0, v=(-0.9, 0.0, 0.0), width=96, height=54), synth.disc(3.0, 20.0)),
+]
+
+
+@pytest.mark.parametrize("uploaded", [False, True])
+@pytest.mark.parametrize("k", range(len(DELAY_CAMS)))
+def test_render_hit_delays(ctx, orc, orc_tables_t, orc_colour, gpu_tables, uploaded, k):
+    """Retarded-time delays of the disc hits (debug channels 16, 17) against
+    the oracle's TRACERAY with the time channels stored in FP32 like the GPU's."""
+    cam, disc = DELAY_CAMS[k]
+    D, U, DT, UT = orc_tables_t
+    Ct, dl = orc_colour
+    f32 = lambda a: a.astype(np.float32)
+    scene = orc.SceneTables(f32(D), f32(U), f32(Ct), f32(dl), DT=f32(DT), UT=f32(UT))
+    t = gpu_tables
+    if uploaded:
+        t = bh.bh_tables_upload(ctx, D, U, bh.BH_F32)
+        bh.bh_tables_upload_time(t, DT, UT)
+    try:
+        _, gd = gpu_render(ctx, t, None, cam, disc)
+    finally:
+        if uploaded:
+            bh.bh_tables_free(t)
+    _, od, _ = orc.render(cam, disc, scene, exposure_stars=EXPOSURE_STARS, debug=True)
+    mask = oracle_mask(od)
+    same = ~mask & (gd[..., 3] == od[..., 3])
+    nsel = 0
+    for h in (0, 1):
+        sel = same & (od[..., 3] >= h + 1)
+        if not sel.any():
+            continue
+        nsel += sel.sum()
+        g, o = gd[..., 16 + h][sel], od[..., 23 + h][sel]
+        # light leaves the disc before it reaches the camera
+        assert (o > 0).all() and (g > 0).all()
+        rel = np.abs(g - o) / np.maximum(np.abs(o), 1.0)
+        assert rel.max() <= HIT_U_REL, (h, rel.max())
+    assert nsel > 0
+    # no hit: zero delays
+    none = gd[..., 3] == 0
+    assert (gd[..., 16][none] == 0).all() and (gd[..., 17][none] == 0).all()
+
+
 @pytest.mark.parametrize("cam", [
     synth.camera(6.0, 85.0, v=(0.0, 0.0, 0.5), width=192, height=108),
     synth.camera(3.2, 89.0, v=(-0.9, 0.0, 0.0), width=96, height=54),
@@ -302,6 +381,32 @@ def test_batch_equals_single(ctx, gpu_tables, static_scene):
         bh.bh_render(ctx, gpu_tables, cube, c, disc, sh, single)
         torch.cuda.synchronize()
         assert torch.equal(single, o)
+
+
+def test_autotune_every_candidate_same_image(gpu_tables, static_scene):
+    """The autotuner launches every candidate launch shape; the image does not
+    depend on the shape, and batched renders stay equal to single ones."""
+    cube, _ = static_scene
+    c2 = bh.bh_create(0, 0)
+    try:
+        cams = synth.batch_cameras(4, seed=1, resolutions=((64, 48), (33, 17), (128, 72)))
+        disc = synth.disc()
+        sh = bh.make_shading(1.0, EXPOSURE_STARS)
+        before = []
+        for c in cams:
+            o = torch.zeros((c["height"], c["width"], 4), device="cuda")
+            bh.bh_render(c2, gpu_tables, cube, c, disc, sh, o)
+            before.append(o)
+        outs = [torch.zeros_like(o) for o in before]
+        choice = bh.bh_autotune_batch(c2, gpu_tables, cube, cams, disc, sh, outs)
+        assert choice >= 0
+        outs = [torch.zeros_like(o) for o in before]
+        bh.bh_render_batch(c2, gpu_tables, cube, cams, disc, sh, outs)
+        torch.cuda.synchronize()
+        for b, o in zip(before, outs):
+            assert torch.equal(b, o)
+    finally:
+        bh.bh_destroy(c2)
 
 
 def test_render_to_host_equals_device(ctx, gpu_tables, static_scene):
