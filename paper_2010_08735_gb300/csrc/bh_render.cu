@@ -389,14 +389,16 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         // T^4 ~ u^3 (1 - sqrt(3u)), T = t_peak at the maximum: log2(D T)
         float fu = up * up * up * (1.f - 1.7320508f * su);
         if (fu > 0.f) {
-          float lgT = log2f(Dk) + lg_tpeak + 0.25f * (log2f(fu) - lg_fmax);
+          // hardware log2 and exp (errors of a few 1e-6 relative at most
+          // here, far below the black-body table's interpolation error)
+          float lgT = __log2f(Dk) + lg_tpeak + 0.25f * (__log2f(fu) - lg_fmax);
           if (lgT >= 8.f) {  // D T >= 256 K
             float f = (lgT - 8.f) * (kDiscN / 12.f) - 0.5f;
             f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
             int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
             float tt = f - k0;
             float4 a = s_disc[k0], b = s_disc[k1];
-            float wy = trans * sc * expf(fmaf(tt, b.x - a.x, a.x));  // (ln Y, X/Y, Z/Y) table
+            float wy = trans * sc * __expf(fmaf(tt, b.x - a.x, a.x));  // (ln Y, X/Y, Z/Y) table
             LX = fmaf(wy, fmaf(tt, b.y - a.y, a.y), LX);
             LY += wy;
             LZ = fmaf(wy, fmaf(tt, b.z - a.z, a.z), LZ);
