@@ -522,8 +522,6 @@ extern "C" void bh_destroy(bh_ctx *c) {
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->cam_host) cudaFreeHost(c->cam_host);
   if (c->cam_dev) cudaFree(c->cam_dev);
-  if (c->tile_host) cudaFreeHost(c->tile_host);
-  if (c->tile_dev) cudaFree(c->tile_dev);
   if (c->frame_dev) cudaFree(c->frame_dev);
   if (c->orb_outs_host) cudaFreeHost(c->orb_outs_host);
   if (c->orb_outs_dev) cudaFree(c->orb_outs_dev);

@@ -88,9 +88,6 @@ struct bh_ctx {
   void *cam_host = nullptr;           // pinned
   void *cam_dev = nullptr;
   int cam_cap = 0;
-  void *tile_host = nullptr;          // pinned
-  void *tile_dev = nullptr;
-  int tile_cap = 0;
   bh::BatchGraph graph;               // bh_render_batch launches
   void *orb_outs_host = nullptr;      // bh_render_orbits: pinned output pointers
   void *orb_outs_dev = nullptr;       // device copy of them, then the tile count
