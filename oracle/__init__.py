@@ -30,7 +30,7 @@ SRC = HERE / "bh_oracle.c"
 LIB = HERE / "liboracle.so"
 
 MU = 4.0 / 27.0
-NDBG = 25
+NDBG = 29
 
 _lib = None
 
@@ -54,7 +54,9 @@ class Camera(C.Structure):
 
 class Disc(C.Structure):
     _fields_ = [("r_in", C.c_double), ("r_out", C.c_double), ("t_peak", C.c_double),
-                ("density", C.c_double), ("enabled", C.c_int)]
+                ("density", C.c_double), ("enabled", C.c_int),
+                ("particles", C.POINTER(C.c_double)), ("n_particles", C.c_int),
+                ("time", C.c_double)]
 
 
 class Scene(C.Structure):
@@ -119,6 +121,11 @@ def lib():
                                      C.POINTER(Scene), C.c_int, C.c_int, C.c_int, C.c_int,
                                      _D, _D, C.POINTER(C.c_longlong)]),
             "orc_bruteforce_ray": (C.c_int, [_D, _D, C.c_double, C.c_double, C.c_double, _D]),
+            "orc_ellipk": (C.c_double, [C.c_double]),
+            "orc_particle_point": (None, [_D, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]),
+            "orc_disc_density": (C.c_double, [_D, C.c_int, C.c_double, C.c_double, C.c_double,
+                                              C.c_double]),
             "orc_orbit_init": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.POINTER(Orbit)]),
             "orc_orbit_advance": (None, [C.POINTER(Orbit), C.c_double, C.c_int]),
@@ -340,9 +347,16 @@ def make_camera(cam: dict) -> Camera:
 
 
 def make_disc(d: dict) -> Disc:
+    """d may carry "particles" ((n, 3): u1, u2, phi0) and "time" (Appendix B)."""
     x = Disc()
     x.r_in, x.r_out, x.t_peak, x.density = d["r_in"], d["r_out"], d["t_peak"], d["density"]
     x.enabled = int(d.get("enabled", 1))
+    parts = d.get("particles")
+    if parts is not None and len(parts):
+        arr = np.ascontiguousarray(parts, dtype=np.float64).reshape(-1, 3)
+        x._keep = arr  # the struct points into it
+        x.particles, x.n_particles = _dp(arr), arr.shape[0]
+    x.time = float(d.get("time", 0.0))
     return x
 
 
@@ -417,16 +431,34 @@ def bruteforce_ray(x0, d0, r_in=3.0, r_out=12.0, step=1e-3):
     """Table-free 3D photon orbit; returns dict(dir, captured, hits_u)."""
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     d0 = np.ascontiguousarray(d0, dtype=np.float64)
-    o = np.zeros(9)
+    o = np.zeros(17)
     lib().orc_bruteforce_ray(_dp(x0), _dp(d0), r_in, r_out, step, _dp(o))
-    n = int(o[4])
-    return {"dir": o[0:3], "captured": bool(o[3]), "hits_u": list(o[5:5 + min(n, 4)]),
-            "n_crossings": n}
+    n = min(int(o[4]), 4)
+    return {"dir": o[0:3], "captured": bool(o[3]), "hits_u": list(o[5:5 + n]),
+            "hits_t": list(o[9:9 + n]), "hits_phi": list(o[13:13 + n]), "n_crossings": int(o[4])}
 
 
 # --------------------------------------------------------------------------
 # Free-fall camera orbit (Appendix C)
 # --------------------------------------------------------------------------
+
+def ellipk(k: float) -> float:
+    """Complete elliptic integral of the first kind K(k) (modulus k)."""
+    return lib().orc_ellipk(k)
+
+
+def particle_point(p, t: float, a: float):
+    """(u, phi) of point a of linear particle p = (u1, u2, phi0) at time t."""
+    u, ph = C.c_double(), C.c_double()
+    arr = np.ascontiguousarray(p, dtype=np.float64)
+    lib().orc_particle_point(_dp(arr), t, a, C.byref(u), C.byref(ph))
+    return u.value, ph.value
+
+
+def disc_density(particles, rho: float, ht: float, hr: float, hphi: float) -> float:
+    arr = np.ascontiguousarray(particles, dtype=np.float64).reshape(-1, 3)
+    return lib().orc_disc_density(_dp(arr), arr.shape[0], rho, ht, hr, hphi)
+
 
 def orbit_init(r0, delta0, v0, chi) -> Orbit:
     o = Orbit()

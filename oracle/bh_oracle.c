@@ -859,6 +859,11 @@ typedef struct {
 typedef struct {
   double r_in, r_out, t_peak, density;
   int enabled;
+  /* animated disc (Appendix B): n_particles linear particles, 3 doubles each
+   * (u1, u2, phi0), and the coordinate time of the frame at the camera */
+  const double *particles;
+  int n_particles;
+  double time;
 } orc_disc;
 
 typedef struct {
@@ -1000,10 +1005,67 @@ double orc_disc_temperature(double t_peak, double u) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Animated disc (Appendix B)                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Complete elliptic integral of the first kind,
+ * K(k) = int_0^1 dx / sqrt((1 - x^2)(1 - k^2 x^2)), by the arithmetic-geometric
+ * mean (Gauss): K(k) = pi / (2 AGM(1, sqrt(1 - k^2))). */
+double orc_ellipk(double k) {
+  double a = 1.0, b = sqrt(1.0 - k * k);
+  for (int it = 0; it < 64 && fabs(a - b) > 1e-16 * a; ++it) {
+    double an = 0.5 * (a + b);
+    b = sqrt(a * b);
+    a = an;
+  }
+  return PI / (2.0 * a);
+}
+
+/* Point a of the linear particle p = (u1, u2, phi0) at coordinate time t, by
+ * the quasi-circular approximation of the precessing massive-particle orbit:
+ * phi_a(t) = a + sqrt(ubar^3 / 2) t + phi0, ubar = (u1 + u2) / 2, and
+ * u_a(t) = u1 + (u2 - u1) sin^2(pi / (4 K) phi_a(t) sqrt(u3 - u1)),
+ * u3 = 1 - u1 - u2, K = K(kappa), kappa^2 = (u2 - u1) / (u3 - u1). */
+void orc_particle_point(const double *p, double t, double a, double *u, double *phi) {
+  double u1 = p[0], u2 = p[1], u3 = 1.0 - u1 - u2;
+  double ub = 0.5 * (u1 + u2);
+  double K = orc_ellipk(sqrt((u2 - u1) / (u3 - u1)));
+  double ph = a + sqrt(0.5 * ub * ub * ub) * t + p[2];
+  double sn = sin(PI / (4.0 * K) * ph * sqrt(u3 - u1));
+  *u = u1 + (u2 - u1) * sn * sn;
+  *phi = ph;
+}
+
+/* Disc density at a hit of coordinate time ht, radius hr and azimuth hphi
+ * (Appendix B, readings C23-C24): for every particle, the parameter of the
+ * nearest point a = (hphi - phi(ht)) mod 2 pi, the "distance" to the
+ * particle centre d^2 = (a/pi - 1)^2 + (hr - 1/u_a(ht))^2 and its
+ * contribution (1 - d^2)^2 for d < 1; the density is rho times the sum,
+ * clamped to 1. */
+double orc_disc_density(const double *particles, int n, double rho, double ht, double hr,
+                        double hphi) {
+  double sum = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double *p = particles + 3 * k;
+    double u0, ph0;
+    orc_particle_point(p, ht, 0.0, &u0, &ph0); /* ph0 = phi(ht) */
+    double a = fmod(hphi - ph0, 2.0 * PI);
+    if (a < 0.0) a += 2.0 * PI;
+    double ua, pha;
+    orc_particle_point(p, ht, a, &ua, &pha);
+    double x = a / PI - 1.0, y = hr - 1.0 / ua;
+    double d2 = x * x + y * y;
+    if (d2 < 1.0) sum += (1.0 - d2) * (1.0 - d2);
+  }
+  double r = rho * sum;
+  return r < 1.0 ? r : 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Per-pixel render                                                          */
 /* ------------------------------------------------------------------------ */
 
-#define NDBG 25
+#define NDBG 29
 typedef struct {
   const orc_camera *cam;
   const orc_disc *disc;
@@ -1167,10 +1229,19 @@ static void render_pixel(render_job *J, int i, int j, pix *quad[2][2], double *o
   /* disc hits, front to back (Sec. 3.3.3, reading C13) */
   double L[3] = {0, 0, 0};
   double trans = 1.0;
-  double rho = J->disc->density;
   double e = sqrt(P->tr[6]);
   for (int h = 0; h < (int)P->tr[1]; ++h) {
     double up = P->tr[2 + 2 * h];
+    /* the hit point: at angle psi from e_x' towards e_y' in the ray plane */
+    double psi = P->tr[3 + 2 * h], hd[3];
+    for (int k = 0; k < 3; ++k) hd[k] = cos(psi) * J->F.rhat[k] + sin(psi) * P->b.ey[k];
+    double hphi = atan2(hd[1], hd[0]);
+    double rho = J->disc->density;
+    if (J->disc->n_particles > 0) /* animated disc: emitted at the retarded time (App. B) */
+      rho = orc_disc_density(J->disc->particles, J->disc->n_particles, J->disc->density,
+                             J->disc->time - P->tr[8 + h], 1.0 / up, hphi);
+    d[25 + h] = rho;
+    d[27 + h] = hphi;
     double T = orc_disc_temperature(J->disc->t_peak, up);
     double D = orc_disc_doppler(P->b.dcam, J->F.u, e, up, P->b.ez[2]);
     d[13 + h] = D;
@@ -1254,7 +1325,8 @@ static void *render_worker(void *argp) {
  *  17 face margin 1 - second/major axis, 18 |det J| / (|J_w| |J_h|),
  *  19 |gradient| of the star sum's Y per pixel of footprint shift, relative
  *     to that sum, 20..22 resulting bound on the change of R, G, B per pixel
- *     of footprint shift, 23..24 retarded times of the two hit slots.
+ *     of footprint shift, 23..24 retarded times of the two hit slots,
+ *  25..26 disc density of the two hit slots, 27..28 their azimuths.
  * force_level >= 0 forces the mip level (for the flat-space checks). */
 int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc,
                double exposure_stars, const orc_scene *sc, int y0, int y1, int force_level,
@@ -1292,37 +1364,46 @@ int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc
 /* x'' = -3/2 h^2 x / |x|^5, h = |x ^ x'| (Cartesian form of Eq. rayequation) */
 /* ------------------------------------------------------------------------ */
 
-static void orbit_deriv(const double *s, double h2, double *ds) {
+/* State: position (0..2), velocity (3..5) with respect to the affine
+ * parameter lambda, and coordinate time (6): along a null geodesic
+ * dt/dlambda = E / (1 - 1/r), with E^2 = |x'|^2 - h^2 / r^3 conserved. */
+static void orbit_deriv(const double *s, double h2, double E, double *ds) {
   double r2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
   double r = sqrt(r2);
   double k = -1.5 * h2 / (r2 * r2 * r);
   ds[0] = s[3]; ds[1] = s[4]; ds[2] = s[5];
   ds[3] = k * s[0]; ds[4] = k * s[1]; ds[5] = k * s[2];
+  ds[6] = E / (1.0 - 1.0 / r);
 }
-static void orbit_rk4(const double *s, double h2, double dl, double *o) {
-  double k1[6], k2[6], k3[6], k4[6], t[6];
-  orbit_deriv(s, h2, k1);
-  for (int a = 0; a < 6; ++a) t[a] = s[a] + 0.5 * dl * k1[a];
-  orbit_deriv(t, h2, k2);
-  for (int a = 0; a < 6; ++a) t[a] = s[a] + 0.5 * dl * k2[a];
-  orbit_deriv(t, h2, k3);
-  for (int a = 0; a < 6; ++a) t[a] = s[a] + dl * k3[a];
-  orbit_deriv(t, h2, k4);
-  for (int a = 0; a < 6; ++a) o[a] = s[a] + dl / 6.0 * (k1[a] + 2 * k2[a] + 2 * k3[a] + k4[a]);
+static void orbit_rk4(const double *s, double h2, double E, double dl, double *o) {
+  double k1[7], k2[7], k3[7], k4[7], t[7];
+  orbit_deriv(s, h2, E, k1);
+  for (int a = 0; a < 7; ++a) t[a] = s[a] + 0.5 * dl * k1[a];
+  orbit_deriv(t, h2, E, k2);
+  for (int a = 0; a < 7; ++a) t[a] = s[a] + 0.5 * dl * k2[a];
+  orbit_deriv(t, h2, E, k3);
+  for (int a = 0; a < 7; ++a) t[a] = s[a] + dl * k3[a];
+  orbit_deriv(t, h2, E, k4);
+  for (int a = 0; a < 7; ++a) o[a] = s[a] + dl / 6.0 * (k1[a] + 2 * k2[a] + 2 * k3[a] + k4[a]);
 }
 
 /* x0: pseudo-Cartesian position, d0: pseudo-Cartesian direction.
- * out: [0..2] escape direction (0 if captured), [3] captured, [4] number of
- * disc crossings with r_in <= r <= r_out (at most 4 recorded), [5..8] their u. */
+ * out (17 doubles): [0..2] escape direction (0 if captured), [3] captured,
+ * [4] number of disc crossings with r_in <= r <= r_out (at most 4 recorded),
+ * [5..8] their u, [9..12] the coordinate time from the camera back to each
+ * crossing, [13..16] the crossing's azimuth atan2(y, x). */
 int orc_bruteforce_ray(const double *x0, const double *d0, double r_in, double r_out,
                        double step, double *out) {
-  double s[6];
+  double s[7];
   double dn = norm3(d0);
   for (int a = 0; a < 3; ++a) { s[a] = x0[a]; s[3 + a] = d0[a] / dn; }
+  s[6] = 0.0;
   double hv[3];
   cross3(s, s + 3, hv);
   double h2 = hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2];
-  for (int a = 0; a < 9; ++a) out[a] = 0.0;
+  double r0 = norm3(x0);
+  double E = sqrt(1.0 - h2 / (r0 * r0 * r0)); /* |x'| = 1 at the start */
+  for (int a = 0; a < 17; ++a) out[a] = 0.0;
   int nh = 0;
   for (long it = 0; it < 50000000L; ++it) {
     double r = norm3(s);
@@ -1335,24 +1416,28 @@ int orc_bruteforce_ray(const double *x0, const double *d0, double r_in, double r
     }
     double dl = step * r;
     if (r < 2.0 && dl > step * (r - 1.0) + 1e-6) dl = step * (r - 1.0) + 1e-6;
-    double n[6];
-    orbit_rk4(s, h2, dl, n);
+    double n[7];
+    orbit_rk4(s, h2, E, dl, n);
     if ((s[2] > 0.0) != (n[2] > 0.0) && s[2] != 0.0) {
       /* disc plane crossing: bisection on the step length */
-      double lo = 0.0, hi = dl, m[6];
+      double lo = 0.0, hi = dl, m[7];
       for (int k = 0; k < 100; ++k) {
         double mid = 0.5 * (lo + hi);
-        orbit_rk4(s, h2, mid, m);
+        orbit_rk4(s, h2, E, mid, m);
         if ((m[2] > 0.0) == (s[2] > 0.0)) lo = mid; else hi = mid;
       }
-      orbit_rk4(s, h2, 0.5 * (lo + hi), m);
+      orbit_rk4(s, h2, E, 0.5 * (lo + hi), m);
       double rc = norm3(m);
       if (rc >= r_in && rc <= r_out) {
-        if (nh < 4) out[5 + nh] = 1.0 / rc;
+        if (nh < 4) {
+          out[5 + nh] = 1.0 / rc;
+          out[9 + nh] = m[6];
+          out[13 + nh] = atan2(m[1], m[0]);
+        }
         ++nh;
       }
     }
-    for (int a = 0; a < 6; ++a) s[a] = n[a];
+    for (int a = 0; a < 7; ++a) s[a] = n[a];
   }
   out[4] = nh;
   return 0;

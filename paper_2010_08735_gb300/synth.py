@@ -52,6 +52,19 @@ def disc(r_in=3.0, r_out=12.0, t_peak=1e4, density=0.5, enabled=True) -> dict:
             "density": float(density), "enabled": bool(enabled)}
 
 
+def disc_particles(n=64, seed=5, r_in=3.0, r_out=12.0) -> np.ndarray:
+    """Linear particles of the animated disc (Appendix B), (n, 3) float64 rows
+    (u1, u2, phi0): mean radius uniform on [r_in + 1/2, r_out - 1/2],
+    eccentricity uniform on [0, 0.05] (u1, u2 = ubar (1 -+ ecc)), phase uniform
+    on [0, 2 pi)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rbar = rng.uniform(r_in + 0.5, r_out - 0.5, n)
+    ecc = rng.uniform(0.0, 0.05, n)
+    phi0 = rng.uniform(0.0, 2.0 * np.pi, n)
+    ub = 1.0 / rbar
+    return np.stack([ub * (1.0 - ecc), ub * (1.0 + ecc), phi0], axis=1)
+
+
 # The five workloads: 256^2 static; 1080p orbiting at 0.5c; 4K infalling at
 # 0.9c; a 64-camera batch; 256 served viewers.
 WORKLOADS = {
