@@ -204,12 +204,35 @@ typedef struct {
   int width, height;    /* pixels, 1..16384 each */
 } bh_camera;
 
+typedef struct bh_particles bh_particles;
+
 typedef struct {
   double r_in, r_out; /* 3 <= r_in < r_out; disc in the z = 0 plane, prograde about +z */
   double t_peak_K;    /* temperature at r = 49/12, where T^4 ~ u^3 (1 - sqrt(3u)) peaks */
   double density;     /* in [0,1]: emission weight and opacity of each disc crossing */
   int enabled;
+  /* Animated disc (Appendix B), or NULL for the constant density above.  With
+   * particles, the density of a crossing is min(1, density * sum_p f_p), f_p
+   * the contribution of linear particle p at the crossing's retarded time
+   * time - delay (delay from the tables' time channels, which must be set),
+   * radius and azimuth. */
+  const bh_particles *particles;
+  double time;        /* coordinate time of the frame at the camera */
 } bh_disc;
+
+/* Linear particles of the animated disc (Appendix B): n rows of 3 doubles
+ * (u1, u2, phi0), 0 < u1 <= u2 <= 1/3, 1 <= n <= 256.  Each row is a
+ * quasi-circular precessing orbit, phi(t) = sqrt(ubar^3/2) t + phi0 with
+ * ubar = (u1 + u2)/2, u(phi) = u1 + (u2 - u1) sin^2(pi/(4K) phi sqrt(u3 - u1)),
+ * u3 = 1 - u1 - u2, K the complete elliptic integral of the first kind of
+ * modulus sqrt((u2 - u1)/(u3 - u1)).  A crossing at time t, radius r and
+ * azimuth phi takes a = (phi - phi(t)) mod 2 pi, d^2 = (a/pi - 1)^2 +
+ * (r - 1/u(a + phi(t)))^2 and f = (1 - d^2)^2 for d < 1, else 0.  The rows
+ * are copied to device memory (sorted by radius); invalid rows give
+ * BH_ERR_INVALID_ARG. */
+bh_status bh_disc_particles_create(bh_ctx *ctx, const double *particles_host, int n,
+                                   bh_particles **out);
+void bh_disc_particles_free(bh_particles *p);
 
 typedef struct {
   float exposure_disc;  /* disc radiance scale: 1 = peak black body of Y = 1 */
@@ -229,7 +252,8 @@ bh_status bh_render(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cube
  * Omega/Omega', star Doppler factor, gathered star X, Y, Z, hit-0 Doppler,
  * hit-1 Doppler, texels visited, then the retarded-time delays of hits 0
  * and 1 (coordinate time from the disc point to the camera along the beam,
- * from the tables' time channels; 0 without a hit) and two zeros. */
+ * from the tables' time channels; 0 without a hit) and the disc densities
+ * of hits 0 and 1 (0 without a hit). */
 bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
                           const bh_camera *camera, const bh_disc *disc,
                           const bh_shading *shading, float *out_rgba_device, float *dbg_device,

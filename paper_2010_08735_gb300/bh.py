@@ -39,7 +39,8 @@ class Camera(C.Structure):
 
 class Disc(C.Structure):
     _fields_ = [("r_in", C.c_double), ("r_out", C.c_double), ("t_peak_K", C.c_double),
-                ("density", C.c_double), ("enabled", C.c_int)]
+                ("density", C.c_double), ("enabled", C.c_int), ("particles", C.c_void_p),
+                ("time", C.c_double)]
 
 
 class Shading(C.Structure):
@@ -81,6 +82,7 @@ def lib():
             "bh_tables_upload": [_vp, P(TableDesc), P(C.c_double), P(C.c_double), _vp, P(_vp)],
             "bh_tables_copy_out": [_vp, P(C.c_double), P(C.c_double)],
             "bh_tables_upload_time": [_vp, P(C.c_double), P(C.c_double), _vp],
+            "bh_disc_particles_create": [_vp, P(C.c_double), C.c_int, P(_vp)],
             "bh_tables_copy_time": [_vp, P(C.c_double), P(C.c_double)],
             "bh_tables_copy_colour": [_vp, P(C.c_float), P(C.c_float)],
             "bh_build_star_cubemap": [_vp, _vp, C.c_longlong, C.c_int, C.c_int, C.c_int, _vp,
@@ -124,6 +126,8 @@ def lib():
         L.bh_tables_free.restype = None
         L.bh_cubemap_free.argtypes = [_vp]
         L.bh_cubemap_free.restype = None
+        L.bh_disc_particles_free.argtypes = [_vp]
+        L.bh_disc_particles_free.restype = None
         _lib = L
     return _lib
 
@@ -176,9 +180,12 @@ def make_camera(cam: dict) -> Camera:
 
 
 def make_disc(d: dict) -> Disc:
+    """d may carry "particles_handle" (from bh_disc_particles_create) and "time"."""
     x = Disc()
     x.r_in, x.r_out, x.t_peak_K, x.density = d["r_in"], d["r_out"], d["t_peak"], d["density"]
     x.enabled = int(d.get("enabled", 1))
+    x.particles = d.get("particles_handle")
+    x.time = float(d.get("time", 0.0))
     return x
 
 
@@ -265,6 +272,19 @@ def bh_tables_copy_time(tables: int, d_n: int, u_ne: int, u_nphi: int):
     _check(lib().bh_tables_copy_time(tables, DT.ctypes.data_as(C.POINTER(C.c_double)),
                                      UT.ctypes.data_as(C.POINTER(C.c_double))))
     return DT, UT
+
+
+def bh_disc_particles_create(ctx: int, particles) -> int:
+    """particles: (n, 3) rows (u1, u2, phi0) of the animated disc."""
+    arr = np.ascontiguousarray(particles, dtype=np.float64).reshape(-1, 3)
+    out = _vp()
+    _check(lib().bh_disc_particles_create(ctx, arr.ctypes.data_as(C.POINTER(C.c_double)), arr.shape[0],
+                                          C.byref(out)))
+    return out.value
+
+
+def bh_disc_particles_free(p: int) -> None:
+    lib().bh_disc_particles_free(p)
 
 
 def bh_tables_copy_colour(tables: int):

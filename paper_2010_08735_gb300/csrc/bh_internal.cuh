@@ -24,6 +24,7 @@ constexpr int kDiscN = 1024;
 constexpr int kNLambda = 95;  // 360..830 nm, 5 nm trapezoid
 constexpr int kNLocus = 4096;
 constexpr int kMaxUTexels = 4096;
+constexpr int kMaxParticles = 256;  // animated disc: shared memory holds 32 bytes per particle
 
 // Status word bits written by kernels (never a trap or an assert).
 constexpr unsigned kStatusMbarTimeout = 1u;
@@ -110,6 +111,12 @@ struct bh_tables {
   float *DT = nullptr, *UT = nullptr;       // their FP32 copies (read by the debug render)
   float4 *C = nullptr;                    // colour shift table [k][j][i] (XYZ, pad)
   float4 *disc = nullptr;                 // ln Y, X/Y, Z/Y of black bodies, log2 T in [8, 20]
+};
+
+struct bh_particles {
+  bh_ctx *ctx = nullptr;
+  int n = 0;
+  double *dev = nullptr;  // 8 doubles per particle, sorted by rmin: u1, u2, phi0, omega, c, rmin, rmax, 0
 };
 
 struct bh_cubemap {

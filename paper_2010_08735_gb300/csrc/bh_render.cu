@@ -11,6 +11,7 @@
 // read-only path; the star cube map is gathered from L2/HBM with 8-byte
 // records.  Pixels leave as one float4 store each (a warp writes four full
 // 128-byte lines).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -49,7 +50,10 @@ struct RenderParams {
   int d_n;
   const void *U;
   int u_ne, u_nphi, u_bytes;
-  const float *DTt, *UTt;   // regularised-time channels of D and U (debug render only)
+  const float *DTt, *UTt;   // regularised-time channels of D and U (debug and animated disc)
+  const double *parts;      // animated disc: 8 doubles per particle (u1, u2, phi0, omega, c, rmin, rmax, 0)
+  int n_parts;              // 0: constant disc density
+  double time;              // coordinate time of the frame at the camera
   const float4 *C;
   const float4 *disc;
   const uint2 *cube;
@@ -103,6 +107,35 @@ __device__ __forceinline__ float d_x(float e2, float em) {
   return 0.5f + sqrtf(fmaxf(-lg, 0.f) * 0.02f);
 }
 
+// Disc density of Appendix B at a hit seen `delay` before the frame's time,
+// at radius hr and azimuth hphi: the sum over linear particles of
+// (1 - d^2)^2, d^2 = (a/pi - 1)^2 + (hr - 1/u_a)^2, a = (hphi - phi(t)) mod
+// 2 pi, times rho, clamped to 1.  Per particle (two float4, sorted by rmin):
+// (rmin, rmax, u1, u2 - u1), (omega, c, phi(time) mod 2 pi, c phi(time) mod pi);
+// only particles with rmin <= hr <= rmax (|hr - 1/u| < 1 possible) count.
+__device__ __forceinline__ float particle_density(const float4 *sp, int n, float rho, float delay, float hr,
+                                                  float hphi) {
+  const float two_pi = 2.f * kPiF, inv_pi = 1.f / kPiF;
+  float sum = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float4 A = sp[2 * k];
+    if (A.x > hr) break;
+    if (hr > A.y) continue;
+    const float4 B = sp[2 * k + 1];
+    float a = hphi - B.z + B.x * delay;  // phi(time - delay) = phi(time) - omega delay
+    a -= two_pi * floorf(a * (1.f / two_pi));
+    const float sn = sinf(fmaf(B.y, a, B.w) - B.y * B.x * delay);
+    const float ua = fmaf(A.w, sn * sn, A.z);
+    const float x = fmaf(a, inv_pi, -1.f), y = hr - 1.f / ua;
+    const float d2 = fmaf(x, x, y * y);
+    if (d2 < 1.f) {
+      const float f = 1.f - d2;
+      sum = fmaf(f, f, sum);
+    }
+  }
+  return fminf(rho * sum, 1.f);
+}
+
 #ifndef BH_RENDER_MIN_BLOCKS
 #define BH_RENDER_MIN_BLOCKS 4  // resident 256-thread blocks per SM the register budget must allow
 #endif
@@ -112,8 +145,13 @@ __device__ __forceinline__ float byte_to_float(unsigned b) {
   return __uint_as_float(0x4B000000u | b) - 8388608.f;
 }
 
-template <typename DT, bool DEBUG>
+// Kernel variants: plain, animated disc (Appendix B), debug (any disc, plus
+// per-pixel intermediate values).
+enum RenderMode { kPlain = 0, kAnimated = 1, kDebug = 2 };
+
+template <typename DT, int MODE>
 __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const RenderParams P) {
+  constexpr bool DEBUG = MODE == kDebug;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ __align__(8) unsigned long long mbar_never;  // fault injection: nothing arrives
@@ -139,6 +177,18 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst1),
         "l"(P.U), "r"((unsigned)P.u_bytes), "r"(mb)
         : "memory");
+  }
+  // animated disc (Appendix B): this frame's particle constants, phases
+  // reduced in FP64 so that FP32 keeps them exact to ~1e-7 rad at any time
+  float4 *s_part = reinterpret_cast<float4 *>(smem + sizeof(float4) * kDiscN + P.u_bytes);
+  for (int k = threadIdx.x; k < P.n_parts; k += blockDim.x) {
+    const double *q = P.parts + 8 * k;
+    const double Phi = fma(q[3], P.time, q[2]);           // phi(t) = omega t + phi0
+    const double Phir = Phi - 2.0 * kPi * floor(Phi / (2.0 * kPi));
+    const double cPhi = q[4] * Phi;                       // sin^2 has period pi
+    const double S = cPhi - kPi * floor(cPhi / kPi);
+    s_part[2 * k] = make_float4((float)q[5], (float)q[6], (float)q[0], (float)(q[1] - q[0]));
+    s_part[2 * k + 1] = make_float4((float)q[3], (float)q[4], (float)Phir, (float)S);
   }
   __syncthreads();
   bool table_ok;
@@ -258,14 +308,17 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float y0 = z1 * x2 - z2 * x1, y1 = z2 * x0 - z0 * x2;
     bool alpha_ok = false;
     float alpha = 0.f;
+    float tsx = 0.f, tsy = 0.f;  // t in the disc plane (x, y): hits lie at +-t
     {
       float t0 = -z1, t1 = z0;
       float tn = sqrtf(fmaf(t0, t0, t1 * t1));
       if (tn > 1e-12f) {
         // t = +-(e_z ^ e_z')/|.| with t . e_y' >= 0; alpha = angle from e_x' to t
         float ty_ = (t0 * y0 + t1 * y1) / tn, tx_ = (t0 * x0 + t1 * x1) / tn;
-        if (ty_ < 0.f) { ty_ = -ty_; tx_ = -tx_; }
-        alpha = atan2f(ty_, tx_);
+        float sg = ty_ < 0.f ? -1.f : 1.f;
+        alpha = atan2f(sg * ty_, sg * tx_);
+        tsx = sg * t0 / tn;
+        tsy = sg * t1 / tn;
         alpha_ok = true;
       }
     }
@@ -279,7 +332,9 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     bool captured = false;
     int nh = 0;
     float hu0 = 0.f, hu1 = 0.f;
-    float th0 = 0.f, th1 = 0.f;  // retarded-time delays of the hits (debug render)
+    float th0 = 0.f, th1 = 0.f;  // retarded-time delays of the hits (debug render, animated disc)
+    bool odd0 = false, odd1 = false;  // hit at -t rather than +t (an odd number of half turns)
+    const bool anim = MODE == kAnimated || (DEBUG && P.n_parts > 0);
     float delta_p = 0.f, turn = 0.f;  // delta' = delta + turn
     if (em < 0.f && u > 2.f / 3.f) {
       captured = true;
@@ -324,8 +379,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
           return fmaf(ty2, hi - lo, lo);
         };
-        // retarded times (debug only): t = R - 1/u + ln(u/(1-u)) of the
-        // camera point and of the apsis, from the time channel of D
+        // retarded times (debug render and animated disc): t = R - 1/u +
+        // ln(u/(1-u)) of the camera point and of the apsis, from D's time channel
         float tcam = 0.f, tapsis = 0.f;
         auto t_of_R = [](float R, float uu) { return R - 1.f / uu + logf(uu / (1.f - uu)); };
         auto ulookT = [&](float ph) {
@@ -337,26 +392,30 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
           return fmaf(ty2, hi - lo, lo);
         };
-        if (DEBUG) {
+        if (DEBUG || anim) {
           tcam = t_of_R(d_bilinear(P.DTt, dn, fx, yv * (dn - 1), xlo, xhi), u);
           if (em < 0.f) tapsis = t_of_R(d_bilinear(P.DTt, dn, fx, (float)(dn - 1), xlo, xhi), ua);
         }
         float phi = Dl + (s == 1 ? kPiF - delta : delta) + s * alpha;
-        float phi0 = phi - kPiF * floorf(phi / kPiF);
+        float turns0 = floorf(phi / kPiF);
+        float phi0 = phi - kPiF * turns0;
         float u0 = ulook(phi0);
         if (phi0 < phia && P.u_oc <= u0 && u0 <= P.u_ic && ((s == 1 && u0 > u) || (s == -1 && u0 < u))) {
           hu0 = u0;
           nh = 1;
-          if (DEBUG) th0 = (float)s * (t_of_R(ulookT(phi0), u0) - tcam);
+          odd0 = ((int)turns0 & 1) != 0;
+          if (DEBUG || anim) th0 = (float)s * (t_of_R(ulookT(phi0), u0) - tcam);
         }
         if (em < 0.f && s == 1) {
           phi = 2.f * phia - phi;
-          float phi1 = phi - kPiF * floorf(phi / kPiF);
+          float turns1 = floorf(phi / kPiF);
+          float phi1 = phi - kPiF * turns1;
           float u1 = ulook(phi1);
           if (phi1 < phia && P.u_oc <= u1 && u1 <= P.u_ic) {
             float tk = 0.f;
-            if (DEBUG) tk = 2.f * tapsis - tcam - t_of_R(ulookT(phi1), u1);
-            if (nh == 0) { hu0 = u1; th0 = tk; } else { hu1 = u1; th1 = tk; }
+            if (DEBUG || anim) tk = 2.f * tapsis - tcam - t_of_R(ulookT(phi1), u1);
+            const bool odd = ((int)turns1 & 1) != 0;
+            if (nh == 0) { hu0 = u1; th0 = tk; odd0 = odd; } else { hu1 = u1; th1 = tk; odd1 = odd; }
             ++nh;
           }
         }
@@ -372,17 +431,26 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
 
     // ---- disc hits, front to back (Sec. 3.3.3, 3.4.2)
     float LX = 0.f, LY = 0.f, LZ = 0.f, trans = 1.f;
-    float dop0 = 0.f, dop1 = 0.f;
+    float dop0 = 0.f, dop1 = 0.f, dens0 = 0.f, dens1 = 0.f;
     if (nh > 0) {
       // nu/nu' for an emitter on the circular orbit at u' (Eq. Doppler, Eq. k_prime):
       // gamma (1 + beta.d^) / (gamma' (1 + beta'.d^')) sqrt((1-u')/(1-u)) simplifies to
       // dcam sqrt(2 - 3u') / (sqrt(1-u) (sqrt(2) + u'^(3/2) (e_z.e_z') / e)).
       const float ie = rsqrtf(e2);
       const float dpre = dcam * C.inv_sqrt_1mu;
-      const float sc = P.rho * P.exp_disc / y_peak;
+      const float escale = P.exp_disc / y_peak;
       const float lg_tpeak = log2f(P.t_peak), lg_fmax = log2f(P.fmax_disc);
       for (int h = 0; h < nh; ++h) {
         float up = h == 0 ? hu0 : hu1;
+        float rho_h = P.rho;
+        if (anim) {
+          // Appendix B: density at the hit's retarded time, radius and azimuth
+          const float sg = (h == 0 ? odd0 : odd1) ? -1.f : 1.f;
+          rho_h = particle_density(s_part, P.n_parts, P.rho, h == 0 ? th0 : th1, 1.f / up,
+                                   atan2f(sg * tsy, sg * tsx));
+        }
+        if (h == 0) dens0 = rho_h; else dens1 = rho_h;
+        const float sc = rho_h * escale;
         float su = sqrtf(up);
         float Dk = dpre * sqrtf(2.f - 3.f * up) / fmaf(up * su * z2, ie, 1.41421356f);
         if (h == 0) dop0 = Dk; else dop1 = Dk;
@@ -404,7 +472,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
             LZ = fmaf(wy, fmaf(tt, b.z - a.z, a.z), LZ);
           }
         }
-        trans *= 1.f - P.rho;
+        trans *= 1.f - rho_h;
       }
     }
 
@@ -577,7 +645,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         g4[1] = make_float4(hu0, hu1, (float)(anycap ? -1 : level), (float)(anycap ? -1 : face));
         g4[2] = make_float4(omega, dstar, SX, SY);
         g4[3] = make_float4(SZ, dop0, dop1, (float)visited);
-        g4[4] = make_float4(th0, th1, 0.f, 0.f);
+        g4[4] = make_float4(th0, th1, dens0, dens1);
       }
     }
   }
@@ -633,7 +701,79 @@ static bool validate_disc(const bh_disc *d) {
     set_error("disc: density in [0,1] and t_peak_K > 0 required");
     return false;
   }
+  if (d->particles && !std::isfinite(d->time)) {
+    set_error("disc: time must be finite");
+    return false;
+  }
   return true;
+}
+
+// Complete elliptic integral of the first kind K(k) by the arithmetic-
+// geometric mean: K = pi / (2 AGM(1, sqrt(1 - k^2))).
+static double ellipk_agm(double k) {
+  double a = 1.0, b = sqrt(1.0 - k * k);
+  for (int it = 0; it < 64 && fabs(a - b) > 1e-16 * a; ++it) {
+    double an = 0.5 * (a + b);
+    b = sqrt(a * b);
+    a = an;
+  }
+  return kPi / (2.0 * a);
+}
+
+extern "C" bh_status bh_disc_particles_create(bh_ctx *ctx, const double *ph, int n, bh_particles **out) {
+  if (!ctx || !ph || !out) { set_error("bh_disc_particles_create: NULL argument"); return BH_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (n < 1 || n > kMaxParticles) {
+    set_error("bh_disc_particles_create: n = %d, must be 1..%d", n, kMaxParticles);
+    return BH_ERR_INVALID_ARG;
+  }
+  std::vector<double> rows((size_t)n * 8);
+  for (int k = 0; k < n; ++k) {
+    const double u1 = ph[3 * k], u2 = ph[3 * k + 1], phi0 = ph[3 * k + 2];
+    if (!(u1 > 0.0 && u1 <= u2 && u2 <= 1.0 / 3.0) || !std::isfinite(phi0)) {
+      set_error("bh_disc_particles_create: row %d needs 0 < u1 <= u2 <= 1/3 and a finite phase", k);
+      return BH_ERR_INVALID_ARG;
+    }
+    const double u3 = 1.0 - u1 - u2, ub = 0.5 * (u1 + u2);
+    const double K = ellipk_agm(sqrt((u2 - u1) / (u3 - u1)));
+    double *r = &rows[(size_t)k * 8];
+    r[0] = u1;
+    r[1] = u2;
+    r[2] = phi0;
+    r[3] = sqrt(0.5 * ub * ub * ub);          // d phi / dt
+    r[4] = kPi * sqrt(u3 - u1) / (4.0 * K);    // sin^2 argument per radian of phi
+    r[5] = 1.0 / u2 - 1.0;                     // radii a hit can be within 1 of
+    r[6] = 1.0 / u1 + 1.0;
+    r[7] = 0.0;
+  }
+  // sorted by rmin: the density loop stops at the first particle beyond the hit
+  std::vector<int> idx(n);
+  for (int k = 0; k < n; ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return rows[a * 8 + 5] < rows[b * 8 + 5]; });
+  std::vector<double> sorted((size_t)n * 8);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < 8; ++j) sorted[(size_t)k * 8 + j] = rows[(size_t)idx[k] * 8 + j];
+  BH_CUDA(cudaSetDevice(ctx->device));
+  bh_particles *p = new bh_particles();
+  p->ctx = ctx;
+  p->n = n;
+  cudaError_t e = cudaMalloc((void **)&p->dev, sorted.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(p->dev, sorted.data(), sorted.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p->dev);
+    delete p;
+    return cuda_fail(e, "bh_disc_particles_create");
+  }
+  *out = p;
+  return BH_OK;
+}
+
+extern "C" void bh_disc_particles_free(bh_particles *p) {
+  if (!p) return;
+  cudaSetDevice(p->ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(p->dev);
+  delete p;
 }
 
 // Camera frame in FP64: static basis (Eq. staticbasis), boost B(v) (the
@@ -748,6 +888,11 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
   P.u_oc = disc->enabled ? (float)(1.0 / disc->r_out) : 1.f;
   P.t_peak = (float)(disc->t_peak_K > 0 ? disc->t_peak_K : 1e4);
   P.rho = (float)disc->density;
+  if (disc->enabled && disc->particles) {
+    P.parts = disc->particles->dev;
+    P.n_parts = disc->particles->n;
+    P.time = disc->time;
+  }
   P.fmax_disc = (float)(pow(12.0 / 49.0, 3) * (1.0 - sqrt(36.0 / 49.0)));
   P.exp_disc = sh ? sh->exposure_disc : 1.f;
   P.exp_stars = sh ? sh->exposure_stars : 0.01f;
@@ -776,16 +921,25 @@ static int render_grid(const bh_ctx *ctx, long long tiles) {
   return (int)std::min<long long>(need, (long long)ctx->sm_count * ctx->tuning.blocks_per_sm);
 }
 
+static const void *kernel_ptr(bool half, int mode) {
+  if (half)
+    return mode == kDebug      ? (const void *)render_kernel<__half, kDebug>
+           : mode == kAnimated ? (const void *)render_kernel<__half, kAnimated>
+                               : (const void *)render_kernel<__half, kPlain>;
+  return mode == kDebug      ? (const void *)render_kernel<float, kDebug>
+         : mode == kAnimated ? (const void *)render_kernel<float, kAnimated>
+                             : (const void *)render_kernel<float, kPlain>;
+}
+
 static bh_status launch(bh_ctx *ctx, const bh_tables *t, RenderParams &P, bool debug, cudaStream_t s) {
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = render_grid(ctx, P.total_tiles);
   if (grid < 1) return BH_OK;
   bool half = t->desc.storage == BH_F16;
-  if (!half && !debug) render_kernel<float, false><<<grid, threads, smem, s>>>(P);
-  else if (!half && debug) render_kernel<float, true><<<grid, threads, smem, s>>>(P);
-  else if (half && !debug) render_kernel<__half, false><<<grid, threads, smem, s>>>(P);
-  else render_kernel<__half, true><<<grid, threads, smem, s>>>(P);
+  const void *f = kernel_ptr(half, debug ? kDebug : (P.n_parts > 0 ? kAnimated : kPlain));
+  void *args[] = {&P};
+  BH_CUDA(cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s));
   count_launch(ctx);
   BH_CUDA(cudaGetLastError());
   return BH_OK;
@@ -828,10 +982,6 @@ static bh_status ensure_cam_staging(bh_ctx *ctx, int n) {
   return BH_OK;
 }
 
-static const void *kernel_ptr(bool half, bool debug) {
-  if (!half) return debug ? (const void *)render_kernel<float, true> : (const void *)render_kernel<float, false>;
-  return debug ? (const void *)render_kernel<__half, true> : (const void *)render_kernel<__half, false>;
-}
 
 bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
                             const bh_camera *cams, const bh_disc *disc, const bh_shading *sh,
@@ -853,10 +1003,10 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   P.ncams = n;
   P.total_tiles = tiles;
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = render_grid(ctx, P.total_tiles);
   if (grid < 1) return BH_OK;
-  const void *func = kernel_ptr(t->desc.storage == BH_F16, false);
+  const void *func = kernel_ptr(t->desc.storage == BH_F16, P.n_parts > 0 ? kAnimated : kPlain);
   void *args[] = {&P};
   cudaKernelNodeParams kp = {};
   kp.func = const_cast<void *>(func);
@@ -1186,10 +1336,11 @@ extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_
   P.total_tiles = 0;
   P.total_tiles_dev = total_dev;
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = ctx->sm_count * ctx->tuning.blocks_per_sm;
-  if (t->desc.storage == BH_F16) render_kernel<__half, false><<<grid, threads, smem, s>>>(P);
-  else render_kernel<float, false><<<grid, threads, smem, s>>>(P);
+  void *args[] = {&P};
+  const void *f = kernel_ptr(t->desc.storage == BH_F16, P.n_parts > 0 ? kAnimated : kPlain);
+  BH_CUDA(cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s));
   count_launch(ctx);
   BH_CUDA(cudaGetLastError());
   return BH_OK;

@@ -52,7 +52,7 @@ def disc(r_in=3.0, r_out=12.0, t_peak=1e4, density=0.5, enabled=True) -> dict:
             "density": float(density), "enabled": bool(enabled)}
 
 
-def disc_particles(n=64, seed=5, r_in=3.0, r_out=12.0) -> np.ndarray:
+def disc_particles(n=16, seed=5, r_in=3.0, r_out=12.0) -> np.ndarray:
     """Linear particles of the animated disc (Appendix B), (n, 3) float64 rows
     (u1, u2, phi0): mean radius uniform on [r_in + 1/2, r_out - 1/2],
     eccentricity uniform on [0, 0.05] (u1, u2 = ubar (1 -+ ecc)), phase uniform

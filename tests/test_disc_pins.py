@@ -88,8 +88,8 @@ def test_density_closed_forms(orc):
 
 
 def test_particle_recipe_is_valid():
-    p = synth.disc_particles(64, 5, 3.0, 12.0)
-    assert p.shape == (64, 3)
+    p = synth.disc_particles(16, 5, 3.0, 12.0)
+    assert p.shape == (16, 3)
     assert (p[:, 0] <= p[:, 1]).all() and (p[:, 1] <= 1 / 3).all() and (p[:, 0] > 0).all()
 
 
@@ -137,7 +137,7 @@ def test_render_density_channels_consistent(orc, exact_tables, colour_tables):
     Ct, dl = colour_tables
     scene = orc.SceneTables(D, U, Ct, dl, DT=DT, UT=UT)
     cam = synth.camera(10.0, 80.0, width=48, height=48)
-    parts = synth.disc_particles(64, 5, 3.0, 12.0)
+    parts = synth.disc_particles(16, 5, 3.0, 12.0)
     disc = dict(synth.disc(3.0, 12.0), particles=parts, time=250.0)
     _, dbg, _ = orc.render(cam, disc, scene, debug=True, nthreads=4)
     _, dbg0, _ = orc.render(cam, synth.disc(3.0, 12.0), scene, debug=True, nthreads=4)

@@ -272,6 +272,54 @@ def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_sce
     check_rgb(og, oo, od, mask, wk["camera"])
 
 
+ANIM_CAMS = [
+    (synth.WORKLOADS["static_256"]["camera"], synth.WORKLOADS["static_256"]["disc"], 250.0),
+    (synth.camera(6.0, 85.0, v=(0.0, 0.0, 0.5), width=192, height=108), synth.disc(3.0, 12.0), 1.0e4),
+    (synth.camera(25.0, 60.0, phi_deg=40.0, v=(0.2, -0.3, 0.1), width=97, height=61), synth.disc(3.0, 20.0), 37.5),
+]
+
+
+@pytest.mark.parametrize("k", range(len(ANIM_CAMS)))
+def test_render_animated_disc(ctx, orc, orc_tables_t, orc_colour, gpu_tables, static_scene, k):
+    """Animated disc (Appendix B): per-hit densities at the retarded times
+    (debug channels 18, 19) and the image, against the oracle."""
+    cam, disc0, time = ANIM_CAMS[k]
+    cube, scene0 = static_scene
+    D, U, DT, UT = orc_tables_t
+    parts = synth.disc_particles(16, 5, disc0["r_in"], disc0["r_out"])
+    f32 = lambda a: a.astype(np.float32)
+    scene = orc.SceneTables(f32(D), f32(U), scene0.C, scene0.disc_ln, scene0.cube, scene0.cube_n,
+                            scene0.cube_dtype, DT=f32(DT), UT=f32(UT))
+    ph = bh.bh_disc_particles_create(ctx, parts)
+    try:
+        disc = dict(disc0, particles=parts, particles_handle=ph, time=time)
+        og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, cam, disc,
+                                              name=f"anim_{cam['width']}x{cam['height']}")
+    finally:
+        bh.bh_disc_particles_free(ph)
+    check_stages(gd, od, mask)
+    same = ~mask & (gd[..., 3] == od[..., 3])
+    n = 0
+    for h in (0, 1):
+        sel = same & (od[..., 3] >= h + 1)
+        if sel.any():
+            n += sel.sum()
+            err = np.abs(gd[..., 18 + h][sel] - od[..., 25 + h][sel])
+            assert err.max() <= 2e-3, (h, err.max())
+    assert n > 0
+    dens = od[..., 25][od[..., 3] >= 1]
+    assert dens.std() > 0.1 and (dens < 1).mean() > 0.5  # the density varies, mostly unclamped
+    check_rgb(og, oo, od, mask, cam)
+
+
+def test_disc_particles_invalid(ctx):
+    good = synth.disc_particles(4, 5)
+    for bad in (good[:0], np.vstack([good] * 65), np.array([[0.2, 0.1, 0.0]]), np.array([[0.1, 0.4, 0.0]]),
+                np.array([[0.0, 0.1, 0.0]]), np.array([[0.1, 0.1, np.nan]])):
+        with pytest.raises(bh.BhError):
+            bh.bh_disc_particles_create(ctx, bad)
+
+
 DELAY_CAMS = [
     (synth.WORKLOADS["static_256"]["camera"], synth.WORKLOADS["static_256"]["disc"]),
     (synth.camera(25.0, 60.0, phi_deg=40.0, v=(0.2, -0.3, 0.1), width=97, height=61), synth.disc(3.0, 20.0)),
