@@ -124,7 +124,9 @@ __device__ __forceinline__ float particle_density(const float4 *sp, int n, float
     const float4 B = sp[2 * k + 1];
     float a = hphi - B.z + B.x * delay;  // phi(time - delay) = phi(time) - omega delay
     a -= two_pi * floorf(a * (1.f / two_pi));
-    const float sn = sinf(fmaf(B.y, a, B.w) - B.y * B.x * delay);
+    float arg = fmaf(B.y, a, B.w) - B.y * B.x * delay;
+    arg = fmaf(-kPiF, rintf(arg * (1.f / kPiF)), arg);  // sin^2 has period pi: reduce to [-pi/2, pi/2]
+    const float sn = __sinf(arg);                       // where the hardware sine is good to ~5e-7
     const float ua = fmaf(A.w, sn * sn, A.z);
     const float x = fmaf(a, inv_pi, -1.f), y = hr - 1.f / ua;
     const float d2 = fmaf(x, x, y * y);
