@@ -338,6 +338,20 @@ bh_status bh_serve_submit(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap
                           const bh_shading *shading, float *out_rgba_device,
                           unsigned long long *ticket);
 
+/* Serving viewers on device-resident orbits (Appendix C): the request of
+ * `viewer` advances its orbit (*orbit_device: caller-owned device memory, one
+ * bh_orbit per viewer, 8-byte aligned) by dtau of proper time in `steps`
+ * Runge-Kutta steps on the device (steps = 0: no advance), as
+ * bh_orbits_advance does, then renders it at width x height into out_device
+ * (16-byte aligned, width*height*4 floats; the orbit's own size fields are
+ * ignored).  Batching, admission and polling as bh_serve_submit; requests of
+ * one viewer advance its orbit in submission order even when consecutive
+ * batches run on different streams. */
+bh_status bh_serve_submit_orbit(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                                int viewer, bh_orbit *orbit_device, double dtau, int steps, int width,
+                                int height, const bh_disc *disc, const bh_shading *shading,
+                                float *out_device, unsigned long long *ticket);
+
 /* Progress the serving loop and report on a ticket: BH_OK when its frame is
  * finished (latency_ms = submit to completion), BH_ERR_NOT_READY while
  * pending (waits up to timeout_us microseconds first; 0 = do not wait). */

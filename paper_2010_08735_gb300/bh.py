@@ -104,6 +104,8 @@ def lib():
             "bh_serve_submit": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading), _vp,
                                 P(C.c_ulonglong)],
             "bh_serve_poll": [_vp, C.c_ulonglong, C.c_int, P(C.c_double)],
+            "bh_serve_submit_orbit": [_vp, _vp, _vp, C.c_int, _vp, C.c_double, C.c_int, C.c_int, C.c_int,
+                                      P(Disc), P(Shading), _vp, P(C.c_ulonglong)],
             "bh_serve_flush": [_vp],
             "bh_check_status": [_vp, _vp],
             "bh_inject_fault": [_vp, C.c_int],
@@ -445,6 +447,18 @@ def bh_serve_submit(ctx, tables, cube, viewer, camera, disc, shading, out):
     t = C.c_ulonglong(0)
     st = _check(lib().bh_serve_submit(ctx, tables, cube, viewer, C.byref(cam), C.byref(d),
                                       C.byref(shading), _ptr(out), C.byref(t)),
+                allow=(BH_ERR_BUSY,))
+    return st, t.value
+
+
+def bh_serve_submit_orbit(ctx, tables, cube, viewer, orbit_device_ptr, dtau, steps, width, height, disc,
+                          shading, out):
+    """orbit_device_ptr: device address of the viewer's bh_orbit.  Returns
+    (status, ticket) as bh_serve_submit."""
+    d = _as(disc, make_disc)
+    t = C.c_ulonglong(0)
+    st = _check(lib().bh_serve_submit_orbit(ctx, tables, cube, viewer, orbit_device_ptr, dtau, steps, width,
+                                            height, C.byref(d), C.byref(shading), _ptr(out), C.byref(t)),
                 allow=(BH_ERR_BUSY,))
     return st, t.value
 

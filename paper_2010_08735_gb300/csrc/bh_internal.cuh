@@ -69,6 +69,16 @@ struct RenderTuning {
   int blocks_per_sm = 4;     // persistent grid = SMs * blocks_per_sm
 };
 
+// A served frame request on a device-resident orbit (Appendix C): advance
+// *orbit by dtau of proper time in `steps` steps, then render it at
+// width x height into out.
+struct OrbitJob {
+  bh_orbit *orbit;
+  float *out;
+  double dtau;
+  int steps, width, height, pad;
+};
+
 // Tile-scheduler counters: every render launch takes the next pair of a ring
 // (re-armed to zero by the launch's last warp), so launches in flight at once
 // on different streams need distinct pairs: at most kSchedRing of them.

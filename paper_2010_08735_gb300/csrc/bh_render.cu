@@ -1037,6 +1037,7 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
 
 size_t cam_const_size() { return sizeof(CamConst); }
 
+
 // ---------------------------------------------------------------------------
 // Free-fall camera orbits (Appendix C), advanced and turned into camera
 // constants on the device so that a viewer's trajectory never leaves HBM.
@@ -1082,10 +1083,7 @@ __device__ static void orbit_rhs(const bh_orbit &o, const double *y, double *dy)
   dy[3] = 0.5 * (2.0 * l2 * u * u * u - 3.0 * l2 * u * u * u * u - u * u);
 }
 
-__global__ void orbit_advance_kernel(bh_orbit *orbits, int n, double dtau, int steps) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  bh_orbit o = orbits[k];
+__device__ static void orbit_advance_one(bh_orbit &o, double dtau, int steps) {
   double h = dtau / steps;
   for (int s = 0; s < steps; ++s) {
     double y[4] = {o.t, o.r, o.psi, o.rdot}, k1[4], k2[4], k3[4], k4[4], z[4];
@@ -1103,7 +1101,45 @@ __global__ void orbit_advance_kernel(bh_orbit *orbits, int n, double dtau, int s
     o.psi = y[2] + h / 6.0 * (k1[2] + 2 * k2[2] + 2 * k3[2] + k4[2]);
     o.rdot = y[3] + h / 6.0 * (k1[3] + 2 * k2[3] + 2 * k3[3] + k4[3]);
   }
+}
+
+__global__ void orbit_advance_kernel(bh_orbit *orbits, int n, double dtau, int steps) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  bh_orbit o = orbits[k];
+  orbit_advance_one(o, dtau, steps);
   orbits[k] = o;
+}
+
+// Served viewers on device-resident orbits: advance each request's orbit
+// (its own, in place), then its camera constants at the request's image size,
+// then the tile offsets -- one block, ahead of the render launch.
+__global__ void serve_orbit_setup_kernel(const OrbitJob *jobs, int n, CamConst *cams, int *total_tiles) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const OrbitJob j = jobs[k];
+    bh_orbit o = *j.orbit;
+    if (j.steps > 0) {
+      orbit_advance_one(o, j.dtau, j.steps);
+      *j.orbit = o;
+    }
+    o.width = j.width;
+    o.height = j.height;
+    bh_camera c;
+    orbit_to_camera(&o, &c);
+    camera_constants(&c, &cams[k]);
+    cams[k].tiles_x = (j.width + 7) / 8;
+    cams[k].out = reinterpret_cast<float4 *>(j.out);
+    cams[k].dbg = nullptr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tiles = 0;
+    for (int k = 0; k < n; ++k) {
+      cams[k].tile0 = tiles;
+      tiles += cams[k].tiles_x * ((jobs[k].height + 3) / 4);
+    }
+    *total_tiles = tiles;
+  }
 }
 
 // Camera constants of every orbit (one block), then the tile offsets (one
@@ -1129,6 +1165,34 @@ __global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *cons
     *total_tiles = tiles;
   }
 }
+
+// One served batch of orbit requests: jobs staged in pinned memory are
+// copied, set up on the device and rendered in one persistent launch.
+bh_status render_orbit_jobs(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
+                            const OrbitJob *jobs_host, OrbitJob *jobs_dev, void *cams_dev, int *total_dev,
+                            const bh_disc *disc, const bh_shading *sh, cudaStream_t s) {
+  BH_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, sizeof(OrbitJob) * n, cudaMemcpyHostToDevice, s));
+  CamConst *cams = static_cast<CamConst *>(cams_dev);
+  serve_orbit_setup_kernel<<<1, 256, 0, s>>>(jobs_dev, n, cams, total_dev);
+  count_launch(ctx);
+  RenderParams P;
+  fill_params(ctx, t, cube, disc, sh, P);
+  P.cams = cams;
+  P.ncams = n;
+  P.total_tiles = 0;
+  P.total_tiles_dev = total_dev;
+  int threads = 32 * ctx->tuning.warps_per_block;
+  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
+  int grid = ctx->sm_count * ctx->tuning.blocks_per_sm;
+  void *args[] = {&P};
+  const void *f = kernel_ptr(t->desc.storage == BH_F16, P.n_parts > 0 ? kAnimated : kPlain);
+  BH_CUDA(cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, s));
+  count_launch(ctx);
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
+}
+
+bool validate_disc_ext(const bh_disc *d) { return validate_disc(d); }
 
 bh_status validate_batch(int n, const bh_camera *cams, const bh_disc *disc, float *const *outs) {
   if (n < 1 || !cams || !outs) { set_error("batch: n >= 1 cameras and outputs required"); return BH_ERR_INVALID_ARG; }

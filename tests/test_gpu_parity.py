@@ -612,6 +612,66 @@ def test_render_orbits_equals_batch(ctx, gpu_tables, static_scene):
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6)
 
 
+def test_served_orbits_equal_advance_then_render(gpu_tables, static_scene):
+    """Viewers served on device-resident orbits: each request advances the
+    viewer's orbit on the device and renders it; after three rounds the orbits
+    and the frames equal bh_orbits_advance + bh_render_orbits on a copy."""
+    cube, _ = static_scene
+    c2 = bh.bh_create(0, 0)
+    try:
+        host = [bh.bh_orbit_init(r, d, v, chi, None, 1.0, w, h)
+                for (r, d, v, chi, w, h) in [(6.0, 1.5707963, 0.316, 0.3, 64, 48), (9.0, 1.3, 0.35, 0.6, 33, 17),
+                                             (15.0, 2.0, 0.5, 1.2, 96, 64), (7.0, 0.9, 0.2, -0.4, 40, 40)]]
+        raw = bh.orbits_to_bytes(host)
+        served = torch.frombuffer(bytearray(raw), dtype=torch.uint8).cuda()
+        ref = served.clone()
+        size = len(raw) // len(host)
+        disc = synth.disc()
+        sh = bh.make_shading(1.0, EXPOSURE_STARS)
+        outs = [torch.zeros((o.height, o.width, 4), device="cuda") for o in host]
+        refs = [torch.zeros_like(o) for o in outs]
+        def submit_round():
+            tickets = []
+            for v, o in enumerate(host):
+                for _ in range(100000):  # a viewer may hold one queued frame: retry until admitted
+                    st, tk = bh.bh_serve_submit_orbit(c2, gpu_tables, cube, v, served.data_ptr() + v * size, 0.5,
+                                                      4, o.width, o.height, disc, sh, outs[v])
+                    if st == bh.BH_OK:
+                        break
+                    bh.bh_serve_flush(c2)
+                assert st == bh.BH_OK
+                tickets.append(tk)
+            return tickets
+
+        def reference_round():
+            bh.bh_orbits_advance(c2, ref, len(host), 0.5, 4)
+            bh.bh_render_orbits(c2, gpu_tables, cube, len(host), ref, disc, sh, refs)
+            torch.cuda.synchronize()
+
+        for rnd in range(2):  # one round at a time
+            for tk in submit_round():
+                assert bh.bh_serve_poll(c2, tk, 5_000_000)[0] == bh.BH_OK
+            reference_round()
+            for a, b in zip(outs, refs):
+                assert torch.equal(a, b)
+        # three rounds in flight at once on the three launch slots: each viewer's
+        # orbit still advances in order, and its last frame is the third round's
+        tickets = submit_round() + submit_round() + submit_round()
+        for tk in tickets:
+            assert bh.bh_serve_poll(c2, tk, 5_000_000)[0] == bh.BH_OK
+        for _ in range(3):
+            reference_round()
+        torch.cuda.synchronize()
+        for a, b in zip(outs, refs):
+            assert torch.equal(a, b)
+        assert torch.equal(served, ref)
+        with pytest.raises(bh.BhError):
+            bh.bh_serve_submit_orbit(c2, gpu_tables, cube, 0, served.data_ptr() + 1, 0.5, 4, 8, 8, disc, sh,
+                                     outs[0])
+    finally:
+        bh.bh_destroy(c2)
+
+
 def test_bounded_table_wait_reports_timeout(ctx, gpu_tables, static_scene):
     """Failure detection without a GPU fault: the injected table wait runs out,
     the kernel reports it through the status word, and the context renders
