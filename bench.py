@@ -378,34 +378,44 @@ def serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=64, viewers=16):
             "frames": frames, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
-def viewer_camera(v, t):
-    """Camera of a served viewer at time t: a circular orbit (moving along e_phi)
-    or a radial fall (moving along -e_r), from the viewer's seeded parameters."""
-    from paper_2010_08735_gb300 import synth
+# Orientation of a camera on an orbit, rows e_w, e_h, e_d on the boosted
+# (r', chi', psi') axes: looking at the hole (-e_d = -e_r'), e_w along the motion.
+LOOK_AT_HOLE = (0.0, 0.0, 1.0, 0.0, -1.0, 0.0, 1.0, 0.0, 0.0)
+RS_PER_SECOND = 60.0  # served trajectories advance 1 r_s/c of proper time per 60 Hz frame
+
+
+def viewer_orbit(bh, v):
+    """Free-fall orbit (Appendix C) of a served viewer from its seeded
+    parameters: a circular orbit at r0 in a plane inclined by theta - 90 deg, or
+    a fall towards the hole from r0 at the viewer's speed."""
+    import math
     if v["kind"] == "circular":
-        r = v["r0"]
-        cam = synth.camera(r, v["theta"] / synth.DEG, v["phi0"] / synth.DEG + (v["speed"] / r) * t / synth.DEG,
-                           v=(0.0, 0.0, v["speed"]), width=v["width"], height=v["height"])
+        delta0, v0 = math.pi / 2, min(math.sqrt(1.0 / (2.0 * (v["r0"] - 1.0))), 0.95)
     else:
-        r = max(2.0, v["r0"] - v["speed"] * t * 50.0)
-        cam = synth.camera(r, v["theta"] / synth.DEG, v["phi0"] / synth.DEG, v=(-v["speed"], 0.0, 0.0),
-                           width=v["width"], height=v["height"])
-    return cam
+        delta0, v0 = math.pi - 0.02, v["speed"]
+    return bh.bh_orbit_init(v["r0"], delta0, v0, v["theta"] - math.pi / 2, LOOK_AT_HOLE, math.radians(60.0),
+                            v["width"], v["height"])
 
 
 def serve_workload(bh, dev, tables, cube, sh, duration=1.5, viewers=256, rate_hz=60.0,
                    budget=40 << 30):
     """The served workload: `viewers` viewers with Poisson frame requests at
-    rate_hz each (mixed 720p/1080p/4K), admission under a device-memory budget,
-    one disc-parameter change half way that switches new requests to freshly
-    rebuilt tables (frames queued on the old tables finish on them).  Open loop
-    in wall-clock time; reports completed frames/s, Mpix/s, p50/p99 latency and
-    the refused requests."""
+    rate_hz each (mixed 720p/1080p/4K) on free-fall orbits resident on the
+    device (each admitted request advances its viewer's orbit by the proper time
+    since the viewer's last admitted request), admission under a device-memory
+    budget, one disc-parameter change half way that switches new requests to
+    freshly rebuilt tables (frames queued on the old tables finish on them).
+    Open loop in wall-clock time; reports completed frames/s, Mpix/s, p50/p99
+    latency and the refused requests."""
     import torch
     from paper_2010_08735_gb300 import synth
     tr = synth.viewer_traffic(viewers, seed=4, rate_hz=rate_hz, duration_s=duration)
     ctx = bh.bh_create(dev.index or 0, budget)
     vs = tr["viewers"]
+    raw = bh.orbits_to_bytes([viewer_orbit(bh, v) for v in vs])
+    osize = len(raw) // len(vs)
+    orbit_buf = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+    last_t = [0.0] * len(vs)
     bufs = [[torch.empty((v["height"], v["width"], 4), device=dev) for _ in range(2)] for v in vs]
     disc_a, disc_b = synth.disc(3.0, 12.0), synth.disc(3.0, 14.0)
     cur_tables, old_tables = tables, None
@@ -431,11 +441,14 @@ def serve_workload(bh, dev, tables, cube, sh, duration=1.5, viewers=256, rate_hz
             refused += 1  # both of the viewer's frame buffers are still in use
             continue
         out = bufs[vid][slot[vid]]
-        st, tk = bh.bh_serve_submit(ctx, cur_tables, cube, vid, viewer_camera(v, te), disc, sh, out)
+        dtau = RS_PER_SECOND * (te - last_t[vid])
+        st, tk = bh.bh_serve_submit_orbit(ctx, cur_tables, cube, vid, orbit_buf.data_ptr() + vid * osize, dtau,
+                                          8 if dtau > 0 else 0, v["width"], v["height"], disc, sh, out)
         submitted += 1
         if st == bh.BH_OK:
             pending[tk] = (vid, v["width"] * v["height"])
             slot[vid] ^= 1
+            last_t[vid] = te
         else:
             refused += 1
     while pending:
@@ -457,7 +470,7 @@ def serve_workload(bh, dev, tables, cube, sh, duration=1.5, viewers=256, rate_hz
             "mpix_per_s": px_done / 1e6 / el, "frames_1080p_equiv_per_s": px_done / (1920 * 1080) / el,
             "p50_ms": lat[n // 2] if n else None, "p99_ms": lat[min(n - 1, int(0.99 * n))] if n else None,
             "table_rebuilds": 1, "budget_bytes": budget,
-            "mix": "720p/1080p/4K uniform; circular or radial trajectories"}
+            "mix": "720p/1080p/4K uniform; circular or infalling free-fall orbits advanced on the device"}
 
 
 def serve_orbits_run(bh, ctx, tables, cube, wk, sh, dev, frames=2000, viewers=16):
@@ -474,7 +487,7 @@ def serve_orbits_run(bh, ctx, tables, cube, wk, sh, dev, frames=2000, viewers=16
         r0 = float(rng.uniform(5.0, 20.0))
         v0 = math.sqrt(1.0 / (2.0 * (r0 - 1.0))) * float(rng.uniform(0.8, 1.1))  # near circular
         orbits.append(bh.bh_orbit_init(r0, math.pi / 2, min(v0, 0.95), float(rng.uniform(-0.5, 0.5)),
-                                       None, math.radians(60.0), W, H))
+                                       LOOK_AT_HOLE, math.radians(60.0), W, H))
     raw = bh.orbits_to_bytes(orbits)
     size = len(raw) // viewers
     buf = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
