@@ -259,9 +259,10 @@ bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap
                           const bh_shading *shading, float *out_rgba_device, float *dbg_device,
                           void *stream);
 
-/* End-to-end form: render into a context-owned device frame buffer and copy
- * the image to out_rgba_host (width*height*4 floats; pinned memory gives the
- * fastest copy).  Synchronises `stream` before returning. */
+/* End-to-end form: the image lands in out_rgba_host (width*height*4 floats).
+ * Pinned memory the device can address is written by the kernel directly
+ * (the transfer overlaps the rendering); other memory receives a copy of a
+ * context-owned device frame.  Synchronises `stream` before returning. */
 bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
                             const bh_camera *camera, const bh_disc *disc,
                             const bh_shading *shading, float *out_rgba_host, void *stream);

@@ -1232,6 +1232,19 @@ extern "C" bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *t, const bh
   BH_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   size_t bytes = sizeof(float4) * (size_t)cam->width * cam->height;
+  // Pinned host memory the device can address (cudaHostAlloc, cudaHostRegister;
+  // all pinned memory under unified addressing): the kernel stores the image
+  // straight into it over the host link, overlapping the transfer with the
+  // rendering, instead of rendering to device memory and copying afterwards.
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer &&
+      ((uintptr_t)pa.devicePointer & 15) == 0) {
+    bh_status st = render_one(ctx, t, cube, cam, disc, sh, static_cast<float *>(pa.devicePointer), nullptr, s);
+    if (st) return st;
+    BH_CUDA(cudaStreamSynchronize(s));
+    return BH_OK;
+  }
+  cudaGetLastError();  // pageable memory: cudaPointerGetAttributes may have set an error
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (bytes > ctx->frame_cap) {
     BH_CUDA(cudaStreamSynchronize(s));

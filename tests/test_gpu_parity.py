@@ -463,9 +463,12 @@ def test_render_to_host_equals_device(ctx, gpu_tables, static_scene):
     sh = bh.make_shading(1.0, EXPOSURE_STARS)
     dev = torch.zeros((40, 80, 4), device="cuda")
     bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, dev)
-    host = np.zeros((40, 80, 4), dtype=np.float32)
+    host = np.zeros((40, 80, 4), dtype=np.float32)  # pageable: rendered on the device, then copied
     bh.bh_render_to_host(ctx, gpu_tables, cube, cam, synth.disc(), sh, host)
     assert np.array_equal(host, dev.cpu().numpy())
+    pinned = torch.zeros((40, 80, 4), dtype=torch.float32).pin_memory()  # written by the kernel directly
+    bh.bh_render_to_host(ctx, gpu_tables, cube, cam, synth.disc(), sh, pinned)
+    assert torch.equal(pinned, dev.cpu())
 
 
 def test_serve_results_equal_alone(ctx, gpu_tables, static_scene):
