@@ -157,23 +157,18 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ __align__(8) unsigned long long mbar_never;  // fault injection: nothing arrives
-  float4 *s_disc = reinterpret_cast<float4 *>(smem);
-  const DT *s_U = reinterpret_cast<const DT *>(smem + sizeof(float4) * kDiscN);
+  const float4 *s_disc = P.disc;  // black-body table: read through L1 (16 KiB), not staged
+  const DT *s_U = reinterpret_cast<const DT *>(smem);
 
-  // ---- stage U and the disc table into shared memory with the bulk-copy engine
+  // ---- stage U into shared memory with the bulk-copy engine
   unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
   unsigned mb_never = (unsigned)__cvta_generic_to_shared(&mbar_never);
   if (threadIdx.x == 0) {
-    unsigned bytes = (unsigned)(sizeof(float4) * kDiscN + P.u_bytes);
+    unsigned bytes = (unsigned)(P.u_bytes);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_never));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
-    unsigned dst0 = (unsigned)__cvta_generic_to_shared(s_disc);
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst0),
-        "l"(P.disc), "r"((unsigned)(sizeof(float4) * kDiscN)), "r"(mb)
-        : "memory");
     unsigned dst1 = (unsigned)__cvta_generic_to_shared(s_U);
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst1),
@@ -182,7 +177,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
   }
   // animated disc (Appendix B): this frame's particle constants, phases
   // reduced in FP64 so that FP32 keeps them exact to ~1e-7 rad at any time
-  float4 *s_part = reinterpret_cast<float4 *>(smem + sizeof(float4) * kDiscN + P.u_bytes);
+  float4 *s_part = reinterpret_cast<float4 *>(smem + P.u_bytes);
   for (int k = threadIdx.x; k < P.n_parts; k += blockDim.x) {
     const double *q = P.parts + 8 * k;
     const double Phi = fma(q[3], P.time, q[2]);           // phi(t) = omega t + phi0
@@ -935,7 +930,7 @@ static const void *kernel_ptr(bool half, int mode) {
 
 static bh_status launch(bh_ctx *ctx, const bh_tables *t, RenderParams &P, bool debug, cudaStream_t s) {
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
+  size_t smem = P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = render_grid(ctx, P.total_tiles);
   if (grid < 1) return BH_OK;
   bool half = t->desc.storage == BH_F16;
@@ -1005,7 +1000,7 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   P.ncams = n;
   P.total_tiles = tiles;
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
+  size_t smem = P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = render_grid(ctx, P.total_tiles);
   if (grid < 1) return BH_OK;
   const void *func = kernel_ptr(t->desc.storage == BH_F16, P.n_parts > 0 ? kAnimated : kPlain);
@@ -1182,7 +1177,7 @@ bh_status render_orbit_jobs(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   P.total_tiles = 0;
   P.total_tiles_dev = total_dev;
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
+  size_t smem = P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = ctx->sm_count * ctx->tuning.blocks_per_sm;
   void *args[] = {&P};
   const void *f = kernel_ptr(t->desc.storage == BH_F16, P.n_parts > 0 ? kAnimated : kPlain);
@@ -1415,7 +1410,7 @@ extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_
   P.total_tiles = 0;
   P.total_tiles_dev = total_dev;
   int threads = 32 * ctx->tuning.warps_per_block;
-  size_t smem = sizeof(float4) * kDiscN + P.u_bytes + 2 * sizeof(float4) * P.n_parts;
+  size_t smem = P.u_bytes + 2 * sizeof(float4) * P.n_parts;
   int grid = ctx->sm_count * ctx->tuning.blocks_per_sm;
   void *args[] = {&P};
   const void *f = kernel_ptr(t->desc.storage == BH_F16, P.n_parts > 0 ? kAnimated : kPlain);
