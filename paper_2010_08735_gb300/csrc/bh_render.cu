@@ -63,6 +63,7 @@ struct RenderParams {
   long long mask_off[kMaxLevels];
   float u_ic, u_oc, t_peak, rho;
   float fmax_disc;          // max of u^3 (1 - sqrt(3u)), at u = 12/49
+  float lg_t0;              // log2(t_peak) - log2(fmax_disc) / 4: log2 T(u) = lg_t0 + log2(u^3 (1 - sqrt(3u))) / 4
   int disc_on;
   float exp_disc, exp_stars;
   float M[9];               // XYZ -> linear sRGB
@@ -436,7 +437,6 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       const float ie = rsqrtf(e2);
       const float dpre = dcam * C.inv_sqrt_1mu;
       const float escale = P.exp_disc / y_peak;
-      const float lg_tpeak = log2f(P.t_peak), lg_fmax = log2f(P.fmax_disc);
       for (int h = 0; h < nh; ++h) {
         float up = h == 0 ? hu0 : hu1;
         float rho_h = P.rho;
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         if (fu > 0.f) {
           // hardware log2 and exp (errors of a few 1e-6 relative at most
           // here, far below the black-body table's interpolation error)
-          float lgT = __log2f(Dk) + lg_tpeak + 0.25f * (__log2f(fu) - lg_fmax);
+          float lgT = fmaf(0.25f, __log2f(Dk * Dk * Dk * Dk * fu), P.lg_t0);  // log2(D T)
           if (lgT >= 8.f) {  // D T >= 256 K
             float f = (lgT - 8.f) * (kDiscN / 12.f) - 0.5f;
             f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
@@ -571,11 +571,17 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
               Y = __uint_as_float(r.x & 0xffff0000u);
               Z = __uint_as_float(r.y << 16);
             } else {
-              X = __half2float(__ushort_as_half((unsigned short)(r.x & 0xffffu)));
-              Y = __half2float(__ushort_as_half((unsigned short)(r.x >> 16)));
-              Z = __half2float(__ushort_as_half((unsigned short)(r.y & 0xffffu)));
+              __half2 xy2, zp2;
+              memcpy(&xy2, &r.x, 4);
+              memcpy(&zp2, &r.y, 4);
+              const float2 xy = __half22float2(xy2);
+              X = xy.x;
+              Y = xy.y;
+              Z = __low2float(zp2);
             }
-            float wt = fw * fh * lscale;
+            // the level's scale 4^L multiplies the sums once, after the loop
+            // (a power of two: the same result as scaling every weight)
+            const float wt = fw * fh;
             SX = fmaf(wt, X, SX);
             SY = fmaf(wt, Y, SY);
             SZ = fmaf(wt, Z, SZ);
@@ -596,6 +602,9 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
               take(jj, k);
             }
           }
+          SX *= lscale;
+          SY *= lscale;
+          SZ *= lscale;
         }
       }
       dstar = dcam * C.inv_sqrt_1mu;  // static star at infinity: u' = 0
@@ -891,6 +900,7 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
     P.time = disc->time;
   }
   P.fmax_disc = (float)(pow(12.0 / 49.0, 3) * (1.0 - sqrt(36.0 / 49.0)));
+  P.lg_t0 = (float)(log2((double)P.t_peak) - 0.25 * log2(pow(12.0 / 49.0, 3) * (1.0 - sqrt(36.0 / 49.0))));
   P.exp_disc = sh ? sh->exposure_disc : 1.f;
   P.exp_stars = sh ? sh->exposure_stars : 0.01f;
   xyz_to_srgb(P.M);
