@@ -253,7 +253,10 @@ bh_status bh_render(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cube
  * hit-1 Doppler, texels visited, then the retarded-time delays of hits 0
  * and 1 (coordinate time from the disc point to the camera along the beam,
  * from the tables' time channels; 0 without a hit) and the disc densities
- * of hits 0 and 1 (0 without a hit). */
+ * of hits 0 and 1 (0 without a hit).  The debug render is also a checked
+ * build: every table, cube-map and occupancy index is tested before its
+ * access; an index out of range skips the access and makes bh_check_status
+ * return BH_ERR_DEVICE_STATUS. */
 bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
                           const bh_camera *camera, const bh_disc *disc,
                           const bh_shading *shading, float *out_rgba_device, float *dbg_device,

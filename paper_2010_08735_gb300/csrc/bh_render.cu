@@ -84,11 +84,16 @@ constexpr float kPiF = 3.14159265358979f;
 
 // Bilinear D lookup at Appendix A coordinates; x clamped to its branch (C2).
 template <typename DT>
-__device__ __forceinline__ float d_bilinear(const DT *D, int n, float fx, float fy, int xlo, int xhi) {
+__device__ __forceinline__ float d_bilinear(const DT *D, int n, float fx, float fy, int xlo, int xhi,
+                                            unsigned *chk = nullptr) {
   fx = fminf(fmaxf(fx, (float)xlo), (float)xhi);
   fy = fminf(fmaxf(fy, 0.f), (float)(n - 1));
   int i0 = (int)fx, j0 = (int)fy;
   int i1 = min(i0 + 1, xhi), j1 = min(j0 + 1, n - 1);
+  if (chk && !(i0 >= 0 && j0 >= 0 && i1 < n && j1 < n && i0 <= i1 && j0 <= j1)) {
+    atomicOr(chk, kStatusBadIndex);  // checked (debug) render: record and skip the access
+    return 0.f;
+  }
   float tx = fx - i0, ty = fy - j0;
   float a = ld_tab(D, j0 * n + i0), b = ld_tab(D, j0 * n + i1);
   float c = ld_tab(D, j1 * n + i0), d = ld_tab(D, j1 * n + i1);
@@ -155,6 +160,14 @@ enum RenderMode { kPlain = 0, kAnimated = 1, kDebug = 2 };
 template <typename DT, int MODE>
 __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const RenderParams P) {
   constexpr bool DEBUG = MODE == kDebug;
+  // The debug render is also the checked build: every table, cube-map and
+  // occupancy index is tested before its access; a bad one sets a status bit
+  // (bh_check_status) and the access is skipped -- no trap, no fault.
+  unsigned *const chk = DEBUG ? P.status : nullptr;
+  auto check = [&](bool ok) {
+    if (DEBUG && !ok) atomicOr(P.status, kStatusBadIndex);
+    return !DEBUG || ok;
+  };
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ __align__(8) unsigned long long mbar_never;  // fault injection: nothing arrives
@@ -352,14 +365,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float g = ua + u - ua * ua - ua * u - u * u;
         float om = g > 0.f ? udot * udot / (ua * g) : 1.f - u / ua;
         yv = 1.f - sqrtf(fmaxf(om, 0.f));
-        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
-        Da = d_bilinear(D, dn, fx, (float)(dn - 1), xlo, xhi);
+        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
+        Da = d_bilinear(D, dn, fx, (float)(dn - 1), xlo, xhi, chk);
         phia = Da + 0.5f * kPiF;
       } else {
         const float r23 = 0.81649658f, r13 = 0.57735027f;
         float sq = sqrtf(fabsf(um));
         yv = (r23 + (um >= 0.f ? sq : -sq)) / (r23 + r13);
-        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi);
+        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
       }
       if (alpha_ok && P.disc_on) {
         float e = sqrtf(e2);
@@ -372,6 +385,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           float fy = fminf(fmaxf(ph * yk * (P.u_nphi - 1), 0.f), (float)(P.u_nphi - 1));
           int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
           float ty2 = fy - j0;
+          if (!check(j0 >= 0 && j1 < P.u_nphi && ui0 >= 0 && ui1 < P.u_ne)) return 0.f;
           float a = sm_tab(s_U, j0 * P.u_ne + ui0), b = sm_tab(s_U, j0 * P.u_ne + ui1);
           float c = sm_tab(s_U, j1 * P.u_ne + ui0), d = sm_tab(s_U, j1 * P.u_ne + ui1);
           float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
@@ -385,14 +399,15 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           float fy = fminf(fmaxf(ph * yk * (P.u_nphi - 1), 0.f), (float)(P.u_nphi - 1));
           int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
           float ty2 = fy - j0;
+          if (!check(j0 >= 0 && j1 < P.u_nphi && ui0 >= 0 && ui1 < P.u_ne)) return 0.f;
           float a = __ldg(P.UTt + j0 * P.u_ne + ui0), b = __ldg(P.UTt + j0 * P.u_ne + ui1);
           float c = __ldg(P.UTt + j1 * P.u_ne + ui0), d = __ldg(P.UTt + j1 * P.u_ne + ui1);
           float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
           return fmaf(ty2, hi - lo, lo);
         };
         if (DEBUG || anim) {
-          tcam = t_of_R(d_bilinear(P.DTt, dn, fx, yv * (dn - 1), xlo, xhi), u);
-          if (em < 0.f) tapsis = t_of_R(d_bilinear(P.DTt, dn, fx, (float)(dn - 1), xlo, xhi), ua);
+          tcam = t_of_R(d_bilinear(P.DTt, dn, fx, yv * (dn - 1), xlo, xhi, chk), u);
+          if (em < 0.f) tapsis = t_of_R(d_bilinear(P.DTt, dn, fx, (float)(dn - 1), xlo, xhi, chk), ua);
         }
         float phi = Dl + (s == 1 ? kPiF - delta : delta) + s * alpha;
         float turns0 = floorf(phi / kPiF);
@@ -462,6 +477,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
             f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
             int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
             float tt = f - k0;
+            if (!check(k0 >= 0 && k1 < kDiscN)) k0 = k1 = 0;
             float4 a = s_disc[k0], b = s_disc[k1];
             float wy = trans * sc * __expf(fmaf(tt, b.x - a.x, a.x));  // (ln Y, X/Y, Z/Y) table
             LX = fmaf(wy, fmaf(tt, b.y - a.y, a.y), LX);
@@ -535,7 +551,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float cS = S * sL, cT = T * sL, hsL = hs * sL, htL = ht * sL;
         float a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
         float det = a11 * a22 - a12 * a21;
-        if (fabsf(det) > 1e-6f * sqrtf((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22))) {
+        if (fabsf(det) > 1e-6f * sqrtf((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22)) &&
+            check(L >= 0 && L < P.cube_levels && L < kMaxLevels && face >= 0 && face < 6)) {
           float id = 1.f / det;
           float i11 = a22 * id, i12 = -a12 * id, i21 = -a21 * id, i22 = a11 * id;
           int i0 = max((int)floorf(cS - hsL), 0), i1 = min((int)floorf(cS + hsL), NL - 1);
@@ -555,6 +572,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           const unsigned rowbits = nrow <= 0 ? 0u : nrow >= 32 ? 0xffffffffu : (1u << nrow) - 1u;
           // The star at texel (jj, ii) of this level (accumulated into S*).
           auto take = [&](const int jj, const int k) {
+            if (!check(jj >= 0 && jj < NL && i0 + k >= 0 && i0 + k < NL)) return;
             const float dt = (jj - cT) + 0.5f / 256.f;
             const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
             const uint2 *rowp = rec + (long long)jj * NL + i0;
@@ -588,6 +606,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           };
           const bool straddle = b0 + nrow > 32 && w0i + 1 < wpr;
           auto row_bits = [&](const int jj) {
+            if (!check(jj >= 0 && jj < NL && w0i >= 0 && w0i + (straddle ? 1 : 0) < wpr)) return 0u;
             const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
             unsigned long long win = __ldg(mrow);
             if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
@@ -620,6 +639,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
         int i1 = min(i0 + 1, kCnx - 1), j1 = min(j0 + 1, kCny - 1), k1 = min(k0 + 1, kCnd - 1);
         float tx2 = fx - i0, ty2 = fy - j0, tz2 = fz - k0;
+        if (!check(i0 >= 0 && j0 >= 0 && k0 >= 0 && i1 < kCnx && j1 < kCny && k1 < kCnd)) i0 = i1 = j0 = j1 = k0 = k1 = 0;
         float cx = 0.f, cy = 0.f, cz = 0.f;
 #pragma unroll
         for (int cidx = 0; cidx < 8; ++cidx) {

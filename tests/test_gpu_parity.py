@@ -182,6 +182,8 @@ def gpu_render(ctx, tables, cube, cam, disc, debug=True, exposure_stars=EXPOSURE
         dbg = torch.zeros((H, W, bh.NDBG), device="cuda")
         bh.bh_render_debug(ctx, tables, cube, cam, disc, sh, out, dbg)
         torch.cuda.synchronize()
+        # the debug render checks every table, cube-map and occupancy index
+        assert bh.bh_check_status(ctx) == bh.BH_OK
         return out.cpu().numpy(), dbg.cpu().numpy()
     bh.bh_render(ctx, tables, cube, cam, disc, sh, out)
     torch.cuda.synchronize()
