@@ -578,6 +578,7 @@ static bh_status tables_alloc(bh_ctx *ctx, const bh_table_desc *desc, cudaStream
 
 extern "C" bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc, void *stream,
                                           bh_tables **out) {
+  TraceRange trace_("bh_precompute_tables");
   if (!ctx || !out) { set_error("bh_precompute_tables: NULL argument"); return BH_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!valid_desc(desc)) return BH_ERR_INVALID_ARG;
@@ -609,6 +610,7 @@ extern "C" bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc
 
 extern "C" bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, const double *Dh,
                                       const double *Uh, void *stream, bh_tables **out) {
+  TraceRange trace_("bh_tables_upload");
   if (!ctx || !out || !Dh || !Uh) { set_error("bh_tables_upload: NULL argument"); return BH_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!valid_desc(desc)) return BH_ERR_INVALID_ARG;

@@ -185,6 +185,7 @@ extern "C" long long bh_cubemap_records(int N) {
 extern "C" bh_status bh_build_star_cubemap(bh_ctx *ctx, const bh_star *stars, long long n, int N,
                                            bh_dtype storage, int on_device, void *stream,
                                            bh_cubemap **out) {
+  TraceRange trace_("bh_build_star_cubemap");
   if (!ctx || !out || (n > 0 && !stars)) { set_error("bh_build_star_cubemap: NULL argument"); return BH_ERR_INVALID_ARG; }
   *out = nullptr;
   if (n < 0 || N < 1 || N > 8192 || (N & (N - 1))) {

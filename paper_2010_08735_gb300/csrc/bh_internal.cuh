@@ -11,9 +11,20 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bh.h"
 
 namespace bh {
+
+// NVTX range over a C-ABI call (precompute, cube map, render, batch, serve):
+// visible in a profiler's timeline, free when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr double kMu = 4.0 / 27.0;  // max of u^2 (1-u), photon sphere u = 2/3 (Sec. 3.3.1)
 constexpr double kPi = 3.14159265358979323846;

@@ -1239,12 +1239,14 @@ using namespace bh;
 extern "C" bh_status bh_render(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
                                const bh_camera *cam, const bh_disc *disc, const bh_shading *sh,
                                float *out, void *stream) {
+  TraceRange trace_("bh_render");
   return render_one(ctx, t, cube, cam, disc, sh, out, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
                                      const bh_camera *cam, const bh_disc *disc,
                                      const bh_shading *sh, float *out, float *dbg, void *stream) {
+  TraceRange trace_("bh_render_debug");
   if (!dbg) { set_error("bh_render_debug: dbg is NULL"); return BH_ERR_INVALID_ARG; }
   return render_one(ctx, t, cube, cam, disc, sh, out, dbg, (cudaStream_t)stream);
 }
@@ -1252,6 +1254,7 @@ extern "C" bh_status bh_render_debug(bh_ctx *ctx, const bh_tables *t, const bh_c
 extern "C" bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
                                        const bh_camera *cam, const bh_disc *disc,
                                        const bh_shading *sh, float *host, void *stream) {
+  TraceRange trace_("bh_render_to_host");
   if (!ctx || !host || !cam) { set_error("bh_render_to_host: NULL argument"); return BH_ERR_INVALID_ARG; }
   if (!validate_camera(cam, 0)) return BH_ERR_INVALID_ARG;
   BH_CUDA(cudaSetDevice(ctx->device));
@@ -1289,6 +1292,7 @@ extern "C" bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *t, const bh
 extern "C" bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
                                      const bh_camera *cams, const bh_disc *disc,
                                      const bh_shading *sh, float *const *outs, void *stream) {
+  TraceRange trace_("bh_render_batch");
   if (!ctx || !t) { set_error("bh_render_batch: NULL argument"); return BH_ERR_INVALID_ARG; }
   bh_status st = validate_batch(n, cams, disc, outs);
   if (st) return st;
@@ -1306,6 +1310,7 @@ extern "C" bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *t, const bh_c
 extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
                                        int n, const bh_camera *cams, const bh_disc *disc,
                                        const bh_shading *sh, float *const *outs, int *chosen) {
+  TraceRange trace_("bh_autotune_batch");
   if (!ctx || !t) { set_error("bh_autotune_batch: NULL argument"); return BH_ERR_INVALID_ARG; }
   bh_status st = validate_batch(n, cams, disc, outs);
   if (st) return st;
@@ -1383,6 +1388,7 @@ extern "C" bh_status bh_orbit_camera(const bh_orbit *o, bh_camera *out) {
 
 extern "C" bh_status bh_orbits_advance(bh_ctx *ctx, bh_orbit *orbits_device, int n, double dtau, int steps,
                                        void *stream) {
+  TraceRange trace_("bh_orbits_advance");
   if (!ctx || (n > 0 && !orbits_device) || n < 0 || steps < 1) {
     set_error("bh_orbits_advance: bad argument");
     return BH_ERR_INVALID_ARG;
@@ -1398,6 +1404,7 @@ extern "C" bh_status bh_orbits_advance(bh_ctx *ctx, bh_orbit *orbits_device, int
 extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube, int n,
                                       const bh_orbit *orbits_device, const bh_disc *disc,
                                       const bh_shading *sh, float *const *outs, void *stream) {
+  TraceRange trace_("bh_render_orbits");
   if (!ctx || !t || !orbits_device || !outs || n < 1 || n > 1024) {
     set_error("bh_render_orbits: bad argument (1 <= n <= 1024)");
     return BH_ERR_INVALID_ARG;

@@ -131,6 +131,7 @@ static bool same_scene(const Request &a, const Request &b) {
 
 // Retire finished slots and start queued requests on free slots.
 static bh_status progress(bh_ctx *ctx) {
+  TraceRange trace_("bh_serve_progress");
   ServeState *S = ctx->serve;
   for (auto &sl : S->slots) {
     if (!sl.busy) continue;
