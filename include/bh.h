@@ -134,6 +134,20 @@ bh_status bh_tables_upload_time(bh_tables *t, const double *DT_host, const doubl
                                 void *stream);
 bh_status bh_tables_copy_time(const bh_tables *t, double *DT_host, double *UT_host);
 
+/* Checkpoints.  bh_tables_save writes every table of the handle (D, U and
+ * their time channels in FP64, the C and black-body tables) to `path`;
+ * bh_tables_load rebuilds a handle from such a file without recomputing
+ * anything (synchronises `stream`).  bh_cubemap_save / bh_cubemap_load do the
+ * same for a star cube map (records and occupancy mask).  Files carry a magic,
+ * a format version, the sizes, the texel-coordinate convention and an FNV-1a
+ * 64-bit hash of their contents; a file that is truncated, corrupt, of
+ * another version or inconsistent is refused with BH_ERR_INVALID_ARG before
+ * any device memory is allocated. */
+bh_status bh_tables_save(const bh_tables *t, const char *path);
+bh_status bh_tables_load(bh_ctx *ctx, const char *path, void *stream, bh_tables **out);
+bh_status bh_cubemap_save(const bh_cubemap *c, const char *path);
+bh_status bh_cubemap_load(bh_ctx *ctx, const char *path, void *stream, bh_cubemap **out);
+
 /* Copy the colour tables: C as [log2 D][y][x] float4 (XYZ, pad), 64*32*64*4
  * floats; the disc black-body table as 1024 float4 (ln Y, X/Y, Z/Y, pad) at
  * log2 T = 8 + 12 (k + 1/2)/1024.  Either may be NULL.  Synchronises. */

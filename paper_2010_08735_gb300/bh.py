@@ -83,6 +83,10 @@ def lib():
             "bh_tables_copy_out": [_vp, P(C.c_double), P(C.c_double)],
             "bh_tables_upload_time": [_vp, P(C.c_double), P(C.c_double), _vp],
             "bh_disc_particles_create": [_vp, P(C.c_double), C.c_int, P(_vp)],
+            "bh_tables_save": [_vp, C.c_char_p],
+            "bh_tables_load": [_vp, C.c_char_p, _vp, P(_vp)],
+            "bh_cubemap_save": [_vp, C.c_char_p],
+            "bh_cubemap_load": [_vp, C.c_char_p, _vp, P(_vp)],
             "bh_tables_copy_time": [_vp, P(C.c_double), P(C.c_double)],
             "bh_tables_copy_colour": [_vp, P(C.c_float), P(C.c_float)],
             "bh_build_star_cubemap": [_vp, _vp, C.c_longlong, C.c_int, C.c_int, C.c_int, _vp,
@@ -287,6 +291,26 @@ def bh_disc_particles_create(ctx: int, particles) -> int:
 
 def bh_disc_particles_free(p: int) -> None:
     lib().bh_disc_particles_free(p)
+
+
+def bh_tables_save(tables: int, path) -> None:
+    _check(lib().bh_tables_save(tables, str(path).encode()))
+
+
+def bh_tables_load(ctx: int, path, stream=None) -> int:
+    out = _vp()
+    _check(lib().bh_tables_load(ctx, str(path).encode(), _stream(stream), C.byref(out)))
+    return out.value
+
+
+def bh_cubemap_save(cube: int, path) -> None:
+    _check(lib().bh_cubemap_save(cube, str(path).encode()))
+
+
+def bh_cubemap_load(ctx: int, path, stream=None) -> int:
+    out = _vp()
+    _check(lib().bh_cubemap_load(ctx, str(path).encode(), _stream(stream), C.byref(out)))
+    return out.value
 
 
 def bh_tables_copy_colour(tables: int):

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "--expt-relaxed-constexpr", "-I", str(HERE.parent / "include")]
 SOURCES = {"bh_core.cu": [], "bh_cubemap.cu": ["-fmad=false"],
-           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false"], "bh_serve.cu": []}
+           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false"], "bh_serve.cu": [], "bh_io.cu": []}
 
 
 def nvcc() -> str:
@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES.items()))
     tmp = OUT.with_suffix(f".so.tmp{os.getpid()}")
-    cmd = [cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcudart"]
+    cmd = [cc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", str(tmp), *map(str, objs), "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -608,6 +608,30 @@ extern "C" bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc
   return BH_OK;
 }
 
+namespace bh {
+bh_status tables_alloc_public(bh_ctx *ctx, const bh_table_desc *desc, bh_tables **out) {
+  return tables_alloc(ctx, desc, nullptr, out);
+}
+
+// Storage copies of D and U (the table's storage type) and FP32 copies of the
+// time channels from the FP64 values already on the device.
+bh_status tables_convert_storage(bh_ctx *ctx, bh_tables *t, cudaStream_t s) {
+  size_t nd = (size_t)t->desc.d_n * t->desc.d_n, nu = (size_t)t->desc.u_ne * t->desc.u_nphi;
+  if (t->desc.storage == BH_F32) {
+    convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (float *)t->D, nd);
+    convert_kernel<float><<<(nu + 255) / 256, 256, 0, s>>>(t->U64, (float *)t->U, nu);
+  } else {
+    convert_kernel<__half><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (__half *)t->D, nd);
+    convert_kernel<__half><<<(nu + 255) / 256, 256, 0, s>>>(t->U64, (__half *)t->U, nu);
+  }
+  convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->DT64, t->DT, nd);
+  convert_kernel<float><<<(nu + 255) / 256, 256, 0, s>>>(t->UT64, t->UT, nu);
+  count_launch(ctx, 4);
+  BH_CUDA(cudaGetLastError());
+  return BH_OK;
+}
+}  // namespace bh
+
 extern "C" bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, const double *Dh,
                                       const double *Uh, void *stream, bh_tables **out) {
   TraceRange trace_("bh_tables_upload");

@@ -275,6 +275,30 @@ extern "C" bh_status bh_cubemap_copy_out(const bh_cubemap *c, uint16_t *h, long 
   return BH_OK;
 }
 
+namespace bh {
+// An empty map of face size N (all levels and the occupancy mask allocated,
+// contents undefined), for loading from a checkpoint.
+bh_status cubemap_alloc_public(bh_ctx *ctx, int N, bh_dtype storage, bh_cubemap **out) {
+  bh_cubemap *c = new bh_cubemap();
+  c->ctx = ctx;
+  c->n = N;
+  c->levels = cube_levels(N);
+  c->storage = storage;
+  c->records = bh_cubemap_records(N);
+  c->mask_words = mask_level_offset(N, c->levels);
+  cudaError_t e = cudaMalloc((void **)&c->rec, sizeof(uint2) * c->records);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->mask, sizeof(unsigned) * c->mask_words);
+  if (e != cudaSuccess) {
+    cudaFree(c->rec);
+    cudaFree(c->mask);
+    delete c;
+    return cuda_fail(e, "cube map allocation");
+  }
+  *out = c;
+  return BH_OK;
+}
+}  // namespace bh
+
 extern "C" void bh_cubemap_free(bh_cubemap *c) {
   if (!c) return;
   cudaSetDevice(c->ctx->device);

@@ -459,6 +459,52 @@ def test_autotune_every_candidate_same_image(gpu_tables, static_scene):
         bh.bh_destroy(c2)
 
 
+def test_checkpoints_round_trip(ctx, gpu_tables, static_scene, tmp_path):
+    """Tables and cube maps saved to disk load back equal, render the same
+    image, and damaged files are refused before anything is allocated."""
+    cube, _ = static_scene
+    tp, cp = tmp_path / "tables.bht", tmp_path / "cube.bhc"
+    bh.bh_tables_save(gpu_tables, tp)
+    bh.bh_cubemap_save(cube, cp)
+    t2 = bh.bh_tables_load(ctx, tp)
+    c2 = bh.bh_cubemap_load(ctx, cp)
+    try:
+        for a, b in zip(bh.bh_tables_copy_out(gpu_tables, 512, 64, 32) + bh.bh_tables_copy_time(gpu_tables, 512, 64, 32),
+                        bh.bh_tables_copy_out(t2, 512, 64, 32) + bh.bh_tables_copy_time(t2, 512, 64, 32)):
+            assert np.array_equal(a, b)
+        for a, b in zip(bh.bh_tables_copy_colour(gpu_tables), bh.bh_tables_copy_colour(t2)):
+            assert np.array_equal(a, b)
+        assert np.array_equal(bh.bh_cubemap_copy_out(cube, 2048), bh.bh_cubemap_copy_out(c2, 2048))
+        cam = synth.camera(10.0, 80.0, width=96, height=64)
+        sh = bh.make_shading(1.0, EXPOSURE_STARS)
+        a = torch.zeros((64, 96, 4), device="cuda")
+        b = torch.zeros_like(a)
+        bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, a)
+        bh.bh_render(ctx, t2, c2, cam, synth.disc(), sh, b)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+    finally:
+        bh.bh_tables_free(t2)
+        bh.bh_cubemap_free(c2)
+    raw = bytearray(tp.read_bytes())
+    bad = tmp_path / "bad.bht"
+    for damage in ("flip", "truncate", "magic"):
+        d = bytearray(raw)
+        if damage == "flip":
+            d[len(d) // 2] ^= 0x40
+        elif damage == "truncate":
+            d = d[:-100]
+        else:
+            d[0:8] = b"NOTTABLE"
+        bad.write_bytes(bytes(d))
+        with pytest.raises(bh.BhError):
+            bh.bh_tables_load(ctx, bad)
+    with pytest.raises(bh.BhError):
+        bh.bh_cubemap_load(ctx, tp)  # a tables file is not a cube map
+    with pytest.raises(bh.BhError):
+        bh.bh_tables_load(ctx, tmp_path / "missing.bht")
+
+
 def test_render_to_host_equals_device(ctx, gpu_tables, static_scene):
     cube, _ = static_scene
     cam = synth.camera(10.0, 80.0, width=80, height=40)
