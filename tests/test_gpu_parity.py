@@ -588,6 +588,28 @@ def test_full_size_sampled_rows(ctx, orc, orc_tables, orc_colour, gpu_tables, na
     check_rgb(og, oo, od, mask, wk["camera"])
 
 
+@pytest.mark.parametrize("cam", [synth.WORKLOADS["static_256"]["camera"],
+                                 synth.camera(3.2, 89.0, v=(-0.9, 0.0, 0.0), width=96, height=54)])
+def test_render_f16_tables(ctx, orc, orc_tables, orc_colour, static_scene, cam):
+    """The FP16 table path (D read through the read-only path, U staged in shared
+    memory as halves) against the oracle reading the same FP16-rounded tables."""
+    cube, scene32 = static_scene
+    D, U = orc_tables
+    Ct, dl = orc_colour
+    h = lambda a: a.astype(np.float16).astype(np.float64)
+    scene = orc.SceneTables(h(D), h(U), Ct.astype(np.float32), dl.astype(np.float32), scene32.cube,
+                            scene32.cube_n, scene32.cube_dtype)
+    t = bh.bh_precompute_tables(ctx, 512, 64, 32, bh.BH_F16)
+    try:
+        disc = synth.WORKLOADS["static_256"]["disc"]
+        og, gd, oo, od, mask = compare_render(orc, ctx, t, cube, scene, cam, disc,
+                                              name=f"f16_{cam['width']}x{cam['height']}")
+    finally:
+        bh.bh_tables_free(t)
+    check_stages(gd, od, mask)
+    check_rgb(og, oo, od, mask, cam)
+
+
 def test_table_storage_precision_report(ctx, orc, orc_tables, orc_colour, static_scene):
     """Error of the linear-RGB image against the oracle reading FP64 tables, for
     the renderer reading FP32- and FP16-stored tables (the tables' own storage
