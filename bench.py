@@ -43,6 +43,23 @@ FLOP_PER_HIT = 60
 FP32_LANES_PER_SM = 128
 
 
+def max_over_ranks(value: float, device, ws: int) -> float:
+    """The largest of every rank's value (the slowest replica sets the time)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps: int, ws: int, t_max: float) -> float:
+    """Frames/s of the whole job: every one of the ws replicas renders `steps`
+    frames; the job takes as long as its slowest replica."""
+    return ws * steps / t_max
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -271,13 +288,9 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = bh.bh_kernel_launches(ctx) - launches0
     frame_ms = [a.elapsed_time(b) for a, b in evs]
-    t_dev = sum(frame_ms) / 1000.0
-    if ws > 1:
-        tt = torch.tensor([t_dev], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(sum(frame_ms) / 1000.0, dev, ws)
     ms_per_step = 1000.0 * t_dev / args.steps
-    fps = ws * args.steps / t_dev
+    fps = replica_throughput(args.steps, ws, t_dev)
 
     # --- end to end through the C ABI with host buffers (D2H of every frame)
     host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
