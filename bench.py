@@ -251,7 +251,7 @@ def run_ours(args):
 
     out = torch.empty((H, W, 4), device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    # tile shape for this frame size from the autotuner (untimed)
+    # launch shape for this frame size from the autotuner (untimed)
     tuned = bh.bh_autotune_batch(ctx, tables, cube, [cam0], disc, sh, [out])
     # --- work counts for the roofline (one untimed debug render)
     dbg = torch.empty((H, W, bh.NDBG), device=dev)
@@ -600,7 +600,7 @@ def orbit_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
 
 def batch_run(bh, ctx, tables, cube, sh, dev, n=64, reps=5):
     """64 cameras of mixed resolution in one persistent launch; Mpix/s and
-    1080p-equivalent frames/s, after the autotuner picked a tile shape."""
+    1080p-equivalent frames/s, after the autotuner picked a launch shape."""
     import torch
     from paper_2010_08735_gb300 import synth
     cams = synth.batch_cameras(n, seed=1)
