@@ -588,6 +588,36 @@ def test_full_size_sampled_rows(ctx, orc, orc_tables, orc_colour, gpu_tables, na
     check_rgb(og, oo, od, mask, wk["camera"])
 
 
+@pytest.mark.parametrize("name", ["orbit_1080p", "infall_4k"])
+def test_timed_kernel_equals_checked_render_full_size(gpu_tables, name):
+    """The plain kernel, in the launch shape the benchmark times (autotuned on
+    the frame), renders every pixel of the full-size frame exactly as the
+    checked debug render that the sampled-row and small-image tests compare
+    with the oracle."""
+    wk = synth.WORKLOADS[name]
+    cam, disc = wk["camera"], wk["disc"]
+    W, H = cam["width"], cam["height"]
+    c2 = bh.bh_create(0, 0)
+    cube = bh.bh_build_star_cubemap(c2, synth.stars(wk["n_stars"], wk["star_seed"]), wk["cube_n"],
+                                    bh.BH_F16 if wk["cube_dtype"] == "f16" else bh.BH_BF16)
+    try:
+        sh = bh.make_shading(1.0, 0.01)
+        plain = torch.zeros((H, W, 4), device="cuda")
+        bh.bh_autotune_batch(c2, gpu_tables, cube, [cam], disc, sh, [plain])
+        plain.zero_()
+        bh.bh_render(c2, gpu_tables, cube, cam, disc, sh, plain)
+        dbg_out = torch.zeros_like(plain)
+        dbg = torch.zeros((H, W, bh.NDBG), device="cuda")
+        bh.bh_render_debug(c2, gpu_tables, cube, cam, disc, sh, dbg_out, dbg)
+        torch.cuda.synchronize()
+        assert bh.bh_check_status(c2) == bh.BH_OK
+        del dbg
+        assert torch.equal(plain, dbg_out)
+    finally:
+        bh.bh_cubemap_free(cube)
+        bh.bh_destroy(c2)
+
+
 @pytest.mark.parametrize("cam", [synth.WORKLOADS["static_256"]["camera"],
                                  synth.camera(3.2, 89.0, v=(-0.9, 0.0, 0.0), width=96, height=54)])
 def test_render_f16_tables(ctx, orc, orc_tables, orc_colour, static_scene, cam):
