@@ -13,9 +13,11 @@
  * precision, one pixel at a time:
  *   - tables D(e,u) and U(e,phi): Algorithm 1 PRECOMPUTE, but the ray
  *     equation (Eq. rayequation, u'' = 3/2 u^2 - u) is integrated with the
- *     classical fixed-step Runge-Kutta 4 instead of Euler (Sec. 3.3.2 allows
- *     "Runge-Kutta or other methods"), sampled exactly at texel centres of
- *     the Appendix A mappings;
+ *     classical fixed-step Runge-Kutta 4 instead of Euler (Sec. 3.3.2 leaves
+ *     the integrator open), sampled exactly at the texel
+ *     coordinates i/(n-1) of the Appendix A mappings (reading C3), with the
+ *     retarded-time channel of Algorithm 1 carried as the regularised time
+ *     R = t + 1/u - ln(u/(1-u)) (reading C5);
  *   - camera basis and beam direction: Eq. staticbasis, Eq. camerabasis,
  *     Eq. d, Eq. raybasis, Eq. alpha;
  *   - Algorithm 1 TRACERAY with bilinear table lookups;
@@ -24,13 +26,17 @@
  *   - the manually filtered star cube map (Sec. 3.3.2, "Emitted light"):
  *     build with colour sums and luminance-weighted positions, mip level
  *     with at most 9x9 texels, tent weights f(w)f(h);
- *   - C(xy,D) colour-shift table (Sec. 3.4.2).
+ *   - C(xy,D) colour-shift table (Sec. 3.4.2);
+ *   - the animated disc of linear particles on precessing orbits, shaded at
+ *     the retarded time of each crossing (Appendix B);
+ *   - free-fall camera orbits (Appendix C).
  * Where the paper is silent the reading used is listed in the design notes
- * of the repository (readings C1..C21); each is restated at its use below.
+ * of the repository (readings C1..C26); each is restated at its use below.
  *
- * A brute-force, table-free integrator of the 3D photon orbit is included
- * for the table-method error report (Sec. 4: "within 1e-3 of reference
- * values computed without intermediate textures").
+ * A brute-force, table-free integrator of the 3D photon orbit (carrying the
+ * coordinate time along it) is included for the table-method error report
+ * (Sec. 4: TRACERAY's results within 1e-3 of values computed without
+ * intermediate textures).
  *
  * Parity notes: the colour observer (piecewise-Gaussian colour matching
  * functions) and the C(xy,D) chromaticity-to-spectrum choice are project
