@@ -106,6 +106,7 @@ def lib():
             "orc_blackbody_xyz": (None, [C.c_double, _D]),
             "orc_xyz_to_rgb_matrix": (None, [_D]),
             "orc_disc_colour_table": (C.c_int, [C.c_int, _D]),
+            "orc_disc_xyz": (None, [_D, C.c_int, C.c_double, _D]),
             "orc_colour_table": (C.c_int, [C.c_int, C.c_int, C.c_int, _D]),
             "orc_decode16": (C.c_double, [C.c_uint16, C.c_int]),
             "orc_encode16": (C.c_uint16, [C.c_double, C.c_int]),
@@ -278,6 +279,15 @@ def xyz_to_rgb_matrix():
 def disc_colour_table(n: int = 1024):
     o = np.zeros((n, 3))
     lib().orc_disc_colour_table(n, _dp(o))
+    return o
+
+
+def disc_xyz(table: np.ndarray, T: float):
+    """XYZ of the black body at T read from a disc colour table (n, 3) as the
+    render reads it (ln Y, X/Y, Z/Y linear in log2 T; 0 below 256 K)."""
+    t = np.ascontiguousarray(table, dtype=np.float64)
+    o = np.zeros(3)
+    lib().orc_disc_xyz(_dp(t), t.shape[0], T, _dp(o))
     return o
 
 

@@ -538,6 +538,9 @@ static void disc_xyz(const double *tab, int n, double T, double *xyz) {
   xyz[2] = Y * lerp(tab[3 * k0 + 2], tab[3 * k1 + 2], t);
 }
 
+/* For tests: the disc colour table lookup the render uses. */
+void orc_disc_xyz(const double *tab, int n, double T, double *xyz) { disc_xyz(tab, n, T, xyz); }
+
 /* CIE 1960 uv of an XYZ colour. */
 static void uv1960(const double *xyz, double *uv) {
   double den = xyz[0] + 15.0 * xyz[1] + 3.0 * xyz[2];
