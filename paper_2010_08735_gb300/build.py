@@ -4,7 +4,9 @@ Each .cu file compiles in its own nvcc process (in parallel), then one link
 step makes ``paper_2010_08735_gb300/libbh.so``.  The cube-map builder is
 compiled without multiply-add contraction (its FP64 binning arithmetic must
 round exactly as written); the FP32 renderer uses the approximate (2 ulp)
-division and square root.
+division and square root, and is also compiled without contraction: every
+fused multiply-add in it is written out (fmaf), so that the single-camera and
+batched instantiations of the pixel code round identically.
 """
 from __future__ import annotations
 
@@ -23,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "--expt-relaxed-constexpr", "-I", str(HERE.parent / "include")]
 SOURCES = {"bh_core.cu": [], "bh_cubemap.cu": ["-fmad=false"],
-           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false"], "bh_serve.cu": [], "bh_io.cu": []}
+           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false", "-fmad=false"], "bh_serve.cu": [], "bh_io.cu": [], "bh_peaks.cu": []}
 
 
 def nvcc() -> str:

@@ -35,6 +35,7 @@ struct CamConst {
   float half_w, half_h;
   int width, height;
   int tiles_x, tile0;
+  float inv_tiles_x;
   float4 *out;
   float *dbg;
 };
@@ -128,9 +129,9 @@ __device__ __forceinline__ float particle_density(const float4 *sp, int n, float
     if (A.x > hr) break;
     if (hr > A.y) continue;
     const float4 B = sp[2 * k + 1];
-    float a = hphi - B.z + B.x * delay;  // phi(time - delay) = phi(time) - omega delay
-    a -= two_pi * floorf(a * (1.f / two_pi));
-    float arg = fmaf(B.y, a, B.w) - B.y * B.x * delay;
+    float a = fmaf(B.x, delay, hphi - B.z);  // phi(time - delay) = phi(time) - omega delay
+    a = fmaf(-two_pi, floorf(a * (1.f / two_pi)), a);
+    float arg = fmaf(-B.y * B.x, delay, fmaf(B.y, a, B.w));
     arg = fmaf(-kPiF, rintf(arg * (1.f / kPiF)), arg);  // sin^2 has period pi: reduce to [-pi/2, pi/2]
     const float sn = __sinf(arg);                       // where the hardware sine is good to ~5e-7
     const float ua = fmaf(A.w, sn * sn, A.z);
@@ -259,20 +260,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       tile = (int)first;
       tile_end = (int)min(first + P.fetch, (long long)total_tiles);
     }
-    // ---- which camera and which tile of it
-    const CamConst *cp = &P.cam0;
-    if (P.cams) {
-      int lo = 0, hi = P.ncams - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&P.cams[mid].tile0) <= tile) lo = mid; else hi = mid - 1;
-      }
-      cp = P.cams + lo;
-    }
-    const CamConst &C = *cp;
-    int t = tile - C.tile0;
-    ++tile;
-    int ty = t / C.tiles_x, tx = t - ty * C.tiles_x;
+    // ---- which camera and which tile of it.  A single-camera launch reads
+    // its constants straight from the kernel parameters (constant bank); a
+    // batch reads them from global memory.  The pixel work is written once.
+    auto shade = [&](const CamConst &C, const int t) {
+    // tile row by a float reciprocal, corrected by one step (exact: the
+    // quotient is at most 4096, so the rounded product is off by < 1)
+    int ty = __float2int_rz(__int2float_rn(t) * C.inv_tiles_x), tx = t - ty * C.tiles_x;
+    if (tx < 0) { --ty; tx += C.tiles_x; } else if (tx >= C.tiles_x) { ++ty; tx -= C.tiles_x; }
     int px = tx * 8 + lx, py = ty * 4 + ly;
 
     // ---- beam initialisation (Eq. d, Eq. raybasis, Eq. alpha)
@@ -287,13 +282,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float wq = fmaf(C.w[0], qw, fmaf(C.w[1], qh, C.w[2] * qd));
     float dpar;
     if (wq > 0.f) {
-      float x0_ = qh * C.w[2] - qd * C.w[1], x1_ = qd * C.w[0] - qw * C.w[2], x2_ = qw * C.w[1] - qh * C.w[0];
+      float x0_ = fmaf(qh, C.w[2], -qd * C.w[1]), x1_ = fmaf(qd, C.w[0], -qw * C.w[2]),
+            x2_ = fmaf(qw, C.w[1], -qh * C.w[0]);
       float c2 = fmaf(x0_, x0_, fmaf(x1_, x1_, x2_ * x2_));
       dpar = C.gamma * (fmaf(qq, C.inv_gamma2, -c2) / (nq * fmaf(C.beta, nq, wq)));
     } else {
       dpar = C.gamma * fmaf(wq, inv, -C.beta);
     }
-    float p0 = (qw - wq * C.w[0]) * inv, p1 = (qh - wq * C.w[1]) * inv, p2 = (qd - wq * C.w[2]) * inv;
+    float p0 = fmaf(-wq, C.w[0], qw) * inv, p1 = fmaf(-wq, C.w[1], qh) * inv, p2 = fmaf(-wq, C.w[2], qd) * inv;
     float ds0 = fmaf(C.Ot[0], p0, fmaf(C.Ot[1], p1, fmaf(C.Ot[2], p2, dpar * C.vhat[0])));
     float ds1 = fmaf(C.Ot[3], p0, fmaf(C.Ot[4], p1, fmaf(C.Ot[5], p2, dpar * C.vhat[1])));
     float ds2 = fmaf(C.Ot[6], p0, fmaf(C.Ot[7], p1, fmaf(C.Ot[8], p2, dpar * C.vhat[2])));
@@ -303,7 +299,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float d1 = fmaf(C.R[3], ds0, fmaf(C.R[4], ds1, C.R[5] * ds2));
     float d2 = fmaf(C.R[6], ds0, fmaf(C.R[7], ds1, C.R[8] * ds2));
     const float x0 = C.x[0], x1 = C.x[1], x2 = C.x[2];
-    float c0 = x1 * d2 - x2 * d1, c1 = x2 * d0 - x0 * d2, c2 = x0 * d1 - x1 * d0;
+    float c0 = fmaf(x1, d2, -x2 * d1), c1 = fmaf(x2, d0, -x0 * d2), c2 = fmaf(x0, d1, -x1 * d0);
     float cn = sqrtf(fmaf(c0, c0, fmaf(c1, c1, c2 * c2)));
     float cosd = fmaf(x0, d0, fmaf(x1, d1, x2 * d2));
     float dd = sqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
@@ -316,7 +312,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       z0 = c0 * ic; z1 = c1 * ic; z2 = c2 * ic;
     }
     // e_y' = e_z' ^ e_x' (its z component is not needed below)
-    float y0 = z1 * x2 - z2 * x1, y1 = z2 * x0 - z0 * x2;
+    float y0 = fmaf(z1, x2, -z2 * x1), y1 = fmaf(z2, x0, -z0 * x2);
     bool alpha_ok = false;
     float alpha = 0.f;
     float tsx = 0.f, tsy = 0.f;  // t in the disc plane (x, y): hits lie at +-t
@@ -325,7 +321,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       float tn = sqrtf(fmaf(t0, t0, t1 * t1));
       if (tn > 1e-12f) {
         // t = +-(e_z ^ e_z')/|.| with t . e_y' >= 0; alpha = angle from e_x' to t
-        float ty_ = (t0 * y0 + t1 * y1) / tn, tx_ = (t0 * x0 + t1 * x1) / tn;
+        float ty_ = fmaf(t0, y0, t1 * y1) / tn, tx_ = fmaf(t0, x0, t1 * x1) / tn;
         float sg = ty_ < 0.f ? -1.f : 1.f;
         alpha = atan2f(sg * ty_, sg * tx_);
         tsx = sg * t0 / tn;
@@ -358,11 +354,11 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       if (em < 0.f) {
         float eta = -em / kMuF;
         float sa = asinf(sqrtf(fminf(eta, 1.f)));
-        float th = (0.5f * kPiF - 2.f * sa) * (1.f / 3.f);
-        ua = 1.f / 3.f + 2.f / 3.f * sinf(th);
+        float th = fmaf(-2.f, sa, 0.5f * kPiF) * (1.f / 3.f);
+        ua = fmaf(2.f / 3.f, sinf(th), 1.f / 3.f);
         // 1 - u/u_a = (du/dphi)^2 / (u_a g), g = (f(u_a) - f(u))/(u_a - u), f(x) = x^2 - x^3:
         // no cancellation when the camera is near the apsis (du/dphi -> 0)
-        float g = ua + u - ua * ua - ua * u - u * u;
+        float g = fmaf(-u, u, fmaf(-ua, u, fmaf(-ua, ua, ua + u)));
         float om = g > 0.f ? udot * udot / (ua * g) : 1.f - u / ua;
         yv = 1.f - sqrtf(fmaxf(om, 0.f));
         Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
@@ -377,7 +373,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       if (alpha_ok && P.disc_on) {
         float e = sqrtf(e2);
         float ux = 1.f / fmaf(6.f, e2, 1.f);
-        float yk = (1.f + 6.f * e2 * e) / (3.f * (1.f + e2));
+        float yk = fmaf(6.f * e2, e, 1.f) / (3.f * (1.f + e2));
         float fxu = fminf(fmaxf(ux * (P.u_ne - 1), 0.f), (float)(P.u_ne - 1));
         int ui0 = (int)fxu, ui1 = min(ui0 + 1, P.u_ne - 1);
         float utx = fxu - ui0;
@@ -409,10 +405,10 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           tcam = t_of_R(d_bilinear(P.DTt, dn, fx, yv * (dn - 1), xlo, xhi, chk), u);
           if (em < 0.f) tapsis = t_of_R(d_bilinear(P.DTt, dn, fx, (float)(dn - 1), xlo, xhi, chk), ua);
         }
-        float phi = Dl + (s == 1 ? kPiF - delta : delta) + s * alpha;
+        float phi = fmaf((float)s, alpha, Dl + (s == 1 ? kPiF - delta : delta));
         float turns0 = floorf(phi / kPiF);
-        float phi0 = phi - kPiF * turns0;
-        float u0 = ulook(phi0);
+        float phi0 = fmaf(-kPiF, turns0, phi);
+        const float u0 = phi0 < phia ? ulook(phi0) : 0.f;
         if (phi0 < phia && P.u_oc <= u0 && u0 <= P.u_ic && ((s == 1 && u0 > u) || (s == -1 && u0 < u))) {
           hu0 = u0;
           nh = 1;
@@ -420,13 +416,13 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           if (DEBUG || anim) th0 = (float)s * (t_of_R(ulookT(phi0), u0) - tcam);
         }
         if (em < 0.f && s == 1) {
-          phi = 2.f * phia - phi;
+          phi = fmaf(2.f, phia, -phi);
           float turns1 = floorf(phi / kPiF);
-          float phi1 = phi - kPiF * turns1;
-          float u1 = ulook(phi1);
+          float phi1 = fmaf(-kPiF, turns1, phi);
+          const float u1 = phi1 < phia ? ulook(phi1) : 0.f;
           if (phi1 < phia && P.u_oc <= u1 && u1 <= P.u_ic) {
             float tk = 0.f;
-            if (DEBUG || anim) tk = 2.f * tapsis - tcam - t_of_R(ulookT(phi1), u1);
+            if (DEBUG || anim) tk = fmaf(2.f, tapsis, -tcam) - t_of_R(ulookT(phi1), u1);
             const bool odd = ((int)turns1 & 1) != 0;
             if (nh == 0) { hu0 = u1; th0 = tk; odd0 = odd; } else { hu1 = u1; th1 = tk; odd1 = odd; }
             ++nh;
@@ -434,7 +430,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         }
       }
       if (udot > 0.f) {
-        if (em < 0.f) turn = 2.f * Da - Dl;
+        if (em < 0.f) turn = fmaf(2.f, Da, -Dl);
         else captured = true;
       } else {
         turn = Dl;
@@ -464,16 +460,16 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         if (h == 0) dens0 = rho_h; else dens1 = rho_h;
         const float sc = rho_h * escale;
         float su = sqrtf(up);
-        float Dk = dpre * sqrtf(2.f - 3.f * up) / fmaf(up * su * z2, ie, 1.41421356f);
+        float Dk = dpre * sqrtf(fmaf(-3.f, up, 2.f)) / fmaf(up * su * z2, ie, 1.41421356f);
         if (h == 0) dop0 = Dk; else dop1 = Dk;
         // T^4 ~ u^3 (1 - sqrt(3u)), T = t_peak at the maximum: log2(D T)
-        float fu = up * up * up * (1.f - 1.7320508f * su);
+        float fu = up * up * up * fmaf(-1.7320508f, su, 1.f);
         if (fu > 0.f) {
           // hardware log2 and exp (errors of a few 1e-6 relative at most
           // here, far below the black-body table's interpolation error)
           float lgT = fmaf(0.25f, __log2f(Dk * Dk * Dk * Dk * fu), P.lg_t0);  // log2(D T)
           if (lgT >= 8.f) {  // D T >= 256 K
-            float f = (lgT - 8.f) * (kDiscN / 12.f) - 0.5f;
+            float f = fmaf(lgT - 8.f, kDiscN / 12.f, -0.5f);
             f = fminf(fmaxf(f, 0.f), (float)(kDiscN - 1));
             int k0 = (int)f, k1 = min(k0 + 1, kDiscN - 1);
             float tt = f - k0;
@@ -497,7 +493,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     sincosf(turn, &st_, &ct_);
     float idd = 1.f / dd;
     float b0 = d0 * idd, b1 = d1 * idd, b2 = d2 * idd;
-    float n0 = z1 * b2 - z2 * b1, n1 = z2 * b0 - z0 * b2, n2 = z0 * b1 - z1 * b0;
+    float n0 = fmaf(z1, b2, -z2 * b1), n1 = fmaf(z2, b0, -z0 * b2), n2 = fmaf(z0, b1, -z1 * b0);
     float dp0 = captured ? 0.f : fmaf(ct_, b0, st_ * n0);
     float dp1 = captured ? 0.f : fmaf(ct_, b1, st_ * n1);
     float dp2 = captured ? 0.f : fmaf(ct_, b2, st_ * n2);
@@ -515,8 +511,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float omega = 0.f, dstar = 0.f, SX = 0.f, SY = 0.f, SZ = 0.f;
     int level = -1, face = -1, visited = 0;
     if (!anycap && P.cube) {
-      float cq0 = qw1 * qh2 - qw2 * qh1, cq1 = qw2 * qh0 - qw0 * qh2, cq2 = qw0 * qh1 - qw1 * qh0;
-      float cd0 = dw1 * dh2 - dw2 * dh1, cd1 = dw2 * dh0 - dw0 * dh2, cd2 = dw0 * dh1 - dw1 * dh0;
+      float cq0 = fmaf(qw1, qh2, -qw2 * qh1), cq1 = fmaf(qw2, qh0, -qw0 * qh2), cq2 = fmaf(qw0, qh1, -qw1 * qh0);
+      float cd0 = fmaf(dw1, dh2, -dw2 * dh1), cd1 = fmaf(dw2, dh0, -dw0 * dh2), cd2 = fmaf(dw0, dh1, -dw1 * dh0);
       float den = sqrtf(fmaf(cd0, cd0, fmaf(cd1, cd1, cd2 * cd2)));
       if (den > 0.f) {
         omega = sqrtf(fmaf(cq0, cq0, fmaf(cq1, cq1, cq2 * cq2))) / den;
@@ -539,19 +535,28 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float hN = 0.5f * N, ima = 1.f / ma;
         float sr = sc * ima, tr = tc * ima;
         float S = (sr + 1.f) * hN, T = (tr + 1.f) * hN;
-        float Jsw = hN * (dscw - sr * dmaw) * ima, Jsh = hN * (dsch - sr * dmah) * ima;
-        float Jtw = hN * (dtcw - tr * dmaw) * ima, Jth = hN * (dtch - tr * dmah) * ima;
+        float Jsw = hN * fmaf(-sr, dmaw, dscw) * ima, Jsh = hN * fmaf(-sr, dmah, dsch) * ima;
+        float Jtw = hN * fmaf(-tr, dmaw, dtcw) * ima, Jth = hN * fmaf(-tr, dmah, dtch) * ima;
         float hs = fabsf(Jsw) + fabsf(Jsh), ht = fabsf(Jtw) + fabsf(Jth);
         float hm = fmaxf(hs, ht);
+        // smallest level L with 2 hm <= 8 * 2^L (at most 9x9 texels, C17): from
+        // the exponent of hm/4 (exact: every quantity is a power-of-two scale)
         int L = 0;
-        while (L < P.cube_levels - 1 && 2.f * hm > 8.f * (float)(1 << L)) ++L;  // <= 9x9 texels (C17)
+        {
+          const float t4 = 0.25f * hm;
+          if (t4 > 1.f) {
+            const unsigned b = __float_as_uint(t4);
+            L = (int)(b >> 23) - 127 + ((b & 0x7fffffu) != 0u ? 1 : 0);
+          }
+          L = min(L, P.cube_levels - 1);
+        }
         level = L;
         float sL = 1.f / (float)(1 << L);
         int NL = N >> L;
         float cS = S * sL, cT = T * sL, hsL = hs * sL, htL = ht * sL;
         float a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
-        float det = a11 * a22 - a12 * a21;
-        if (fabsf(det) > 1e-6f * sqrtf((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22)) &&
+        float det = fmaf(a11, a22, -a12 * a21);
+        if (fabsf(det) > 1e-6f * sqrtf(fmaf(a11, a11, a21 * a21) * fmaf(a12, a12, a22 * a22)) &&
             check(L >= 0 && L < P.cube_levels && L < kMaxLevels && face >= 0 && face < 6)) {
           float id = 1.f / det;
           float i11 = a22 * id, i12 = -a12 * id, i21 = -a21 * id, i22 = a11 * id;
@@ -567,59 +572,59 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           const int nrow = i1 - i0 + 1;
           const float ds0 = (i0 - cS) + 0.5f / 256.f;
           const int wpr = (NL + 31) >> 5;
-          const unsigned *mrows = P.cube_mask + P.mask_off[L] + (long long)face * NL * wpr;
+          const unsigned *mrows = P.cube_mask + P.mask_off[L] + face * NL * wpr;
           const int w0i = i0 >> 5, b0 = i0 & 31;
           const unsigned rowbits = nrow <= 0 ? 0u : nrow >= 32 ? 0xffffffffu : (1u << nrow) - 1u;
-          // The star at texel (jj, ii) of this level (accumulated into S*).
-          auto take = [&](const int jj, const int k) {
-            if (!check(jj >= 0 && jj < NL && i0 + k >= 0 && i0 + k < NL)) return;
-            const float dt = (jj - cT) + 0.5f / 256.f;
-            const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
-            const uint2 *rowp = rec + (long long)jj * NL + i0;
-            const uint2 r = __ldg(rowp + k);
-            unsigned pw = r.y >> 16;
-            float ps = byte_to_float(pw & 255u), pt = byte_to_float(pw >> 8);
-            float w = fmaf(q11, ps, fmaf(q12, pt, fmaf(i11, (float)k, wrow)));
-            float h = fmaf(q21, ps, fmaf(q22, pt, fmaf(i21, (float)k, hrow)));
-            float fw = 1.f - fabsf(w), fh = 1.f - fabsf(h);
-            if (fw <= 0.f || fh <= 0.f) return;
-            float X, Y, Z;
-            if (P.cube_bf16) {
-              X = __uint_as_float(r.x << 16);
-              Y = __uint_as_float(r.x & 0xffff0000u);
-              Z = __uint_as_float(r.y << 16);
-            } else {
-              __half2 xy2, zp2;
-              memcpy(&xy2, &r.x, 4);
-              memcpy(&zp2, &r.y, 4);
-              const float2 xy = __half22float2(xy2);
-              X = xy.x;
-              Y = xy.y;
-              Z = __low2float(zp2);
-            }
-            // the level's scale 4^L multiplies the sums once, after the loop
-            // (a power of two: the same result as scaling every weight)
-            const float wt = fw * fh;
-            SX = fmaf(wt, X, SX);
-            SY = fmaf(wt, Y, SY);
-            SZ = fmaf(wt, Z, SZ);
-          };
           const bool straddle = b0 + nrow > 32 && w0i + 1 < wpr;
           auto row_bits = [&](const int jj) {
             if (!check(jj >= 0 && jj < NL && w0i >= 0 && w0i + (straddle ? 1 : 0) < wpr)) return 0u;
-            const unsigned *mrow = mrows + (long long)jj * wpr + w0i;
+            const unsigned *mrow = mrows + (jj * wpr + w0i);
             unsigned long long win = __ldg(mrow);
             if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
             return (unsigned)(win >> b0) & rowbits;
           };
+          const bool bf16 = P.cube_bf16;
+          unsigned bits = j0 <= j1 ? row_bits(j0) : 0u;
           for (int jj = j0; jj <= j1; ++jj) {
-            unsigned bits = row_bits(jj);
+            // the next row's occupancy is requested before this row's records
+            const unsigned nbits = jj < j1 ? row_bits(jj + 1) : 0u;
             if (nrow > 0) visited += nrow;
+            const float dt = (jj - cT) + 0.5f / 256.f;
+            const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
+            const uint2 *rowp = rec + (jj * NL + i0);
+            // the stars of this row: texel i0 + k for every occupied k
             while (bits) {
               const int k = __ffs(bits) - 1;
               bits &= bits - 1u;
-              take(jj, k);
+              if (!check(jj >= 0 && jj < NL && i0 + k >= 0 && i0 + k < NL)) continue;
+              const uint2 r = __ldg(rowp + k);
+              const unsigned pw = r.y >> 16;
+              const float ps = byte_to_float(pw & 255u), pt = byte_to_float(pw >> 8);
+              const float w = fmaf(q11, ps, fmaf(q12, pt, fmaf(i11, (float)k, wrow)));
+              const float h = fmaf(q21, ps, fmaf(q22, pt, fmaf(i21, (float)k, hrow)));
+              // tent weight f(w) f(h), 0 outside the footprint
+              const float wt = fmaxf(1.f - fabsf(w), 0.f) * fmaxf(1.f - fabsf(h), 0.f);
+              float X, Y, Z;
+              if (bf16) {
+                X = __uint_as_float(r.x << 16);
+                Y = __uint_as_float(r.x & 0xffff0000u);
+                Z = __uint_as_float(r.y << 16);
+              } else {
+                __half2 xy2, zp2;
+                memcpy(&xy2, &r.x, 4);
+                memcpy(&zp2, &r.y, 4);
+                const float2 xy = __half22float2(xy2);
+                X = xy.x;
+                Y = xy.y;
+                Z = __low2float(zp2);
+              }
+              // the level's scale 4^L multiplies the sums once, after the loop
+              // (a power of two: the same result as scaling every weight)
+              SX = fmaf(wt, X, SX);
+              SY = fmaf(wt, Y, SY);
+              SZ = fmaf(wt, Z, SZ);
             }
+            bits = nbits;
           }
           SX *= lscale;
           SY *= lscale;
@@ -629,27 +634,32 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
       dstar = dcam * C.inv_sqrt_1mu;  // static star at infinity: u' = 0
       float Ssum = SX + SY + SZ;
       if (Ssum > 0.f) {
-        // C(xy, D): trilinear, texel centres, clamped
-        float fx = ((SX / Ssum) - 0.15f) * (kCnx / 0.60f) - 0.5f;
-        float fy = ((SY / Ssum) - 0.15f) * (kCny / 0.35f) - 0.5f;
-        float fz = (log2f(dstar) + 4.f) * (kCnd / 8.f) - 0.5f;
+        // C(xy, D): trilinear, texel centres, clamped.  One base texel and
+        // constant strides (0 at a clamped edge, where the weight is 0);
+        // interpolated along x, then y, then log2 D.
+        const float iS = 1.f / Ssum;
+        float fx = fmaf(SX * iS, kCnx / 0.60f, -(0.15f * kCnx / 0.60f + 0.5f));
+        float fy = fmaf(SY * iS, kCny / 0.35f, -(0.15f * kCny / 0.35f + 0.5f));
+        float fz = fmaf(__log2f(dstar), kCnd / 8.f, 4.f * kCnd / 8.f - 0.5f);
         fx = fminf(fmaxf(fx, 0.f), kCnx - 1.f);
         fy = fminf(fmaxf(fy, 0.f), kCny - 1.f);
         fz = fminf(fmaxf(fz, 0.f), kCnd - 1.f);
         int i0 = (int)fx, j0 = (int)fy, k0 = (int)fz;
-        int i1 = min(i0 + 1, kCnx - 1), j1 = min(j0 + 1, kCny - 1), k1 = min(k0 + 1, kCnd - 1);
-        float tx2 = fx - i0, ty2 = fy - j0, tz2 = fz - k0;
-        if (!check(i0 >= 0 && j0 >= 0 && k0 >= 0 && i1 < kCnx && j1 < kCny && k1 < kCnd)) i0 = i1 = j0 = j1 = k0 = k1 = 0;
-        float cx = 0.f, cy = 0.f, cz = 0.f;
-#pragma unroll
-        for (int cidx = 0; cidx < 8; ++cidx) {
-          int ii = (cidx & 1) ? i1 : i0, jj = (cidx & 2) ? j1 : j0, kk = (cidx & 4) ? k1 : k0;
-          float w = ((cidx & 1) ? tx2 : 1.f - tx2) * ((cidx & 2) ? ty2 : 1.f - ty2) * ((cidx & 4) ? tz2 : 1.f - tz2);
-          float4 cv = __ldg(P.C + ((kk * kCny + jj) * kCnx + ii));
-          cx = fmaf(w, cv.x, cx);
-          cy = fmaf(w, cv.y, cy);
-          cz = fmaf(w, cv.z, cz);
-        }
+        const float tx2 = fx - i0, ty2 = fy - j0, tz2 = fz - k0;
+        const int si = i0 < kCnx - 1 ? 1 : 0, sj = j0 < kCny - 1 ? kCnx : 0;
+        const int sk = k0 < kCnd - 1 ? kCnx * kCny : 0;
+        if (!check(i0 >= 0 && j0 >= 0 && k0 >= 0 && i0 < kCnx && j0 < kCny && k0 < kCnd)) i0 = j0 = k0 = 0;
+        const float4 *cb = P.C + ((k0 * kCny + j0) * kCnx + i0);
+        const float4 c000 = __ldg(cb), c100 = __ldg(cb + si), c010 = __ldg(cb + sj), c110 = __ldg(cb + sj + si);
+        const float4 c001 = __ldg(cb + sk), c101 = __ldg(cb + sk + si), c011 = __ldg(cb + sk + sj),
+                     c111 = __ldg(cb + sk + sj + si);
+        auto lerp3 = [](float t, float4 a, float4 b) {
+          return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), fmaf(t, b.z - a.z, a.z), 0.f);
+        };
+        const float4 cy0 = lerp3(ty2, lerp3(tx2, c000, c100), lerp3(tx2, c010, c110));
+        const float4 cy1 = lerp3(ty2, lerp3(tx2, c001, c101), lerp3(tx2, c011, c111));
+        const float4 cc = lerp3(tz2, cy0, cy1);
+        const float cx = cc.x, cy = cc.y, cz = cc.z;
         float sc = Ssum * omega * P.exp_stars * trans;
         LX = fmaf(sc, cx, LX);
         LY = fmaf(sc, cy, LY);
@@ -673,6 +683,22 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         g4[3] = make_float4(SZ, dop0, dop1, (float)visited);
         g4[4] = make_float4(th0, th1, dens0, dens1);
       }
+    }
+    };
+    if (P.cams) {
+      int lo = 0, hi = P.ncams - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&P.cams[mid].tile0) <= tile) lo = mid; else hi = mid - 1;
+      }
+      const CamConst &Cb = P.cams[lo];
+      const int t = tile - Cb.tile0;
+      ++tile;
+      shade(Cb, t);
+    } else {
+      const int t = tile - P.cam0.tile0;
+      ++tile;
+      shade(P.cam0, t);
     }
   }
   // Retire the warp; the last warp of the grid re-arms the counters for the
@@ -986,6 +1012,7 @@ static bh_status render_one(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   fill_params(ctx, t, cube, disc, sh, P);
   camera_constants(cam, &P.cam0);
   P.cam0.tiles_x = tiles_across(cam->width);
+  P.cam0.inv_tiles_x = 1.f / (float)P.cam0.tiles_x;
   P.cam0.tile0 = 0;
   P.cam0.out = reinterpret_cast<float4 *>(out);
   P.cam0.dbg = dbg;
@@ -1021,6 +1048,7 @@ bh_status render_batch_impl(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *c
   for (int k = 0; k < n; ++k) {
     camera_constants(&cams[k], &h[k]);
     h[k].tiles_x = tiles_across(cams[k].width);
+    h[k].inv_tiles_x = 1.f / (float)h[k].tiles_x;
     h[k].tile0 = tiles;
     h[k].out = reinterpret_cast<float4 *>(outs[k]);
     h[k].dbg = nullptr;
@@ -1153,6 +1181,7 @@ __global__ void serve_orbit_setup_kernel(const OrbitJob *jobs, int n, CamConst *
     orbit_to_camera(&o, &c);
     camera_constants(&c, &cams[k]);
     cams[k].tiles_x = (j.width + 7) / 8;
+    cams[k].inv_tiles_x = 1.f / (float)cams[k].tiles_x;
     cams[k].out = reinterpret_cast<float4 *>(j.out);
     cams[k].dbg = nullptr;
   }
@@ -1177,6 +1206,7 @@ __global__ void orbit_camconst_kernel(const bh_orbit *orbits, int n, float *cons
     orbit_to_camera(&orbits[k], &c);
     camera_constants(&c, &cams[k]);
     cams[k].tiles_x = (c.width + 7) / 8;  // 8 x 4 pixel warp tiles
+    cams[k].inv_tiles_x = 1.f / (float)cams[k].tiles_x;
     cams[k].out = reinterpret_cast<float4 *>(outs[k]);
     cams[k].dbg = nullptr;
   }
@@ -1317,7 +1347,8 @@ extern "C" bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *t, const bh
   BH_CUDA(cudaSetDevice(ctx->device));
   // candidates: warps per block, warp tiles per fetch, resident blocks per SM
   static const RenderTuning cand[] = {{8, 1, 4}, {8, 2, 4}, {8, 4, 4}, {8, 8, 4},
-                                      {4, 1, 8}, {4, 2, 8}, {4, 4, 8}, {8, 16, 4}};
+                                      {4, 1, 8}, {4, 2, 8}, {4, 4, 8}, {8, 16, 4},
+                                      {4, 1, 9}, {4, 2, 9}};
   const int nc = sizeof(cand) / sizeof(cand[0]);
   cudaStream_t s;
   BH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
