@@ -83,6 +83,16 @@ bh_status bh_check_status(bh_ctx *ctx, void *stream);
 #define BH_FAULT_TABLE_WAIT 1
 bh_status bh_inject_fault(bh_ctx *ctx, int kind);
 
+/* Issue rates of the SMs of CUDA device `device`, measured by the library's
+ * own microbenchmark kernels (independent dependency chains on every SM; the
+ * paper has no counterpart -- these are the denominators of the render
+ * kernel's roofline).  out[0]: scalar FP32 FMA results per SM per clock;
+ * out[1]: FMA results per SM per clock issued as packed f32x2 FMAs; out[2]:
+ * special-function (reciprocal square root) results per SM per clock;
+ * out[3]: the SM count; out[4]: the SM clock seen during the measurement, MHz.
+ * out holds 5 doubles.  Synchronises the device; allocates a few bytes. */
+bh_status bh_measure_issue_rates(int device, double *out);
+
 /* ------------------------------------------------------------------------ */
 /* Tables D(e,u), U(e,phi) (Algorithm 1 PRECOMPUTE, Sec. 3.3.2-3.3.3,        */
 /* Appendix A) and the colour tables (Sec. 3.4.2)                             */
@@ -188,9 +198,12 @@ bh_status bh_build_star_cubemap(bh_ctx *ctx, const bh_star *stars, long long n, 
  *  - face_size: power of two, at most 128 (the size of the library's static
  *    scratch array, about 6.9 MB, held on every GPU that loads the library
  *    until the process exits); larger sizes return BH_ERR_INVALID_ARG.
- *  - Works on the current CUDA device and needs no bh_ctx.  The first call on
- *    a device looks up the scratch array's device address; make that first
- *    call before any stream capture.
+ *  - Works on the current CUDA device and needs no bh_ctx; `stream`, the
+ *    stars and the records must all belong to that device.  Each call that is
+ *    not under stream capture looks up the scratch array's device address on
+ *    that device; a call under capture reuses the address the device's last
+ *    uncaptured call found, so make one call before capturing (a first call
+ *    under capture returns BH_ERR_INVALID_ARG).
  *  - Allocates nothing (no cudaMalloc, cudaFree or allocating library call).
  *    Every call shares the one scratch array, so calls whose work overlaps
  *    on the GPU (other streams, other threads) race: serialise them.
@@ -372,7 +385,12 @@ bh_status bh_serve_submit_orbit(bh_ctx *ctx, const bh_tables *tables, const bh_c
 
 /* Progress the serving loop and report on a ticket: BH_OK when its frame is
  * finished (latency_ms = submit to completion), BH_ERR_NOT_READY while
- * pending (waits up to timeout_us microseconds first; 0 = do not wait). */
+ * pending (waits up to timeout_us microseconds first; 0 = do not wait).
+ * The serving loop has no thread of its own: queued requests are launched
+ * only inside bh_serve_submit, bh_serve_submit_orbit, bh_serve_poll and
+ * bh_serve_flush.  A client that submits and then stops calling leaves its
+ * queued (not yet launched) frames waiting; poll or flush to keep work
+ * moving. */
 bh_status bh_serve_poll(bh_ctx *ctx, unsigned long long ticket, int timeout_us,
                         double *latency_ms);
 

@@ -112,6 +112,7 @@ def lib():
                                       P(Disc), P(Shading), _vp, P(C.c_ulonglong)],
             "bh_serve_flush": [_vp],
             "bh_check_status": [_vp, _vp],
+            "bh_measure_issue_rates": [C.c_int, P(C.c_double)],
             "bh_inject_fault": [_vp, C.c_int],
         }
         for name, args in sig.items():
@@ -227,6 +228,14 @@ BH_FAULT_TABLE_WAIT = 1
 def bh_check_status(ctx: int, stream=None) -> int:
     """BH_OK, or raises BhError (BH_ERR_TIMEOUT / BH_ERR_DEVICE_STATUS)."""
     return _check(lib().bh_check_status(ctx, _stream(stream)))
+
+
+def bh_measure_issue_rates(device: int = 0) -> dict:
+    """SM issue rates measured by the library's microbenchmark kernels."""
+    o = (C.c_double * 5)()
+    _check(lib().bh_measure_issue_rates(device, o))
+    return {"fp32_fma_per_sm_clk": o[0], "ffma2_fma_per_sm_clk": o[1], "mufu_per_sm_clk": o[2],
+            "sms": int(o[3]), "sm_mhz": o[4]}
 
 
 def bh_inject_fault(ctx: int, kind: int = BH_FAULT_TABLE_WAIT) -> None:
@@ -346,8 +355,14 @@ def bh_build_star_cubemap_noalloc(stars, face_size: int, storage, records, strea
     """Allocation-free cube-map build: stars is a (n, 5) float32 CUDA tensor,
     records a caller-owned CUDA tensor of bh_cubemap_records(face_size) x 4
     uint16 (or int16); face_size <= 128.  Runs on the current device."""
+    import torch
     assert stars.is_cuda and stars.is_contiguous() and stars.shape[-1] == 5
-    assert records.is_cuda and records.numel() >= 4 * bh_cubemap_records(face_size)
+    assert stars.dtype == torch.float32, "stars must be float32 (bh_star: dir[3], lum, temp_K)"
+    assert records.is_cuda and records.is_contiguous() and records.element_size() == 2
+    assert records.numel() >= 4 * bh_cubemap_records(face_size)
+    cur = torch.cuda.current_device()
+    assert stars.device.index == cur and records.device.index == cur, \
+        "stars and records must be on the current CUDA device"
     _check(lib().bh_build_star_cubemap_noalloc(stars.data_ptr() if stars.shape[0] else None,
                                                stars.shape[0], face_size, storage,
                                                records.data_ptr(), _stream(stream)))
