@@ -330,10 +330,13 @@ constexpr size_t kNoAllocScratchWords = 5 * kNoAllocTexels0 + 3 * kNoAllocTexels
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchWords];
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the host-side name of a __device__ array is not a device
-// address).
-static bh_status noalloc_scratch(int device, unsigned long long **out) {
+// Device address of the scratch array on the current device (the host-side
+// name of a __device__ array is not a device address).  Looked up on every
+// call that is not being captured into a CUDA graph, so that a device or
+// primary-context reset between calls cannot leave a stale address behind;
+// a call under stream capture uses the address its device's last uncaptured
+// call found (cudaGetSymbolAddress may load the module, which capture forbids).
+static bh_status noalloc_scratch(int device, bool capturing, unsigned long long **out) {
   static std::mutex mu;
   static unsigned long long *addr[64] = {nullptr};
   if (device < 0 || device >= 64) {
@@ -341,11 +344,15 @@ static bh_status noalloc_scratch(int device, unsigned long long **out) {
     return BH_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lk(mu);
-  if (!addr[device]) {
+  if (!capturing) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "bh_build_star_cubemap_noalloc: cudaGetSymbolAddress");
     addr[device] = static_cast<unsigned long long *>(p);
+  } else if (!addr[device]) {
+    set_error("bh_build_star_cubemap_noalloc: the first call on device %d is under stream capture; "
+              "make one call before capturing", device);
+    return BH_ERR_INVALID_ARG;
   }
   *out = addr[device];
   return BH_OK;
@@ -371,10 +378,12 @@ extern "C" bh_status bh_build_star_cubemap_noalloc(const bh_star *stars_device, 
   }
   int dev = 0;
   BH_CUDA(cudaGetDevice(&dev));
-  unsigned long long *scratch = nullptr;
-  bh_status st = noalloc_scratch(dev, &scratch);
-  if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  BH_CUDA(cudaStreamIsCapturing(s, &cap));
+  unsigned long long *scratch = nullptr;
+  bh_status st = noalloc_scratch(dev, cap != cudaStreamCaptureStatusNone, &scratch);
+  if (st) return st;
   long long nt0 = 6LL * N * N;
   unsigned long long *acc = scratch;
   long long *sums0 = reinterpret_cast<long long *>(scratch + 5 * kNoAllocTexels0);

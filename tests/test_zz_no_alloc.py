@@ -31,10 +31,18 @@ def reference_records(ctx, stars, N, dtype):
 
 
 def test_noalloc_cubemap_matches_allocating_build_twice():
+    """Calls in a row on the one static scratch array, each against the
+    allocating build: a full-size face, then the same face size with fewer
+    stars (the accumulators must have been cleared, not summed onto), another
+    storage type, an empty star list at face size 1 (no mip levels, NULL star
+    pointer) and a few stars at face size 1."""
     ctx = bh.bh_create(0, 0)
     try:
         calls = [(synth.stars(20000, seed=21), 128, bh.BH_F16),
-                 (synth.stars(3000, seed=22), 64, bh.BH_BF16)]
+                 (synth.stars(3000, seed=23), 128, bh.BH_F16),
+                 (synth.stars(3000, seed=22), 64, bh.BH_BF16),
+                 (np.zeros((0, 5), dtype=np.float32), 1, bh.BH_F16),
+                 (synth.stars(5, seed=24), 1, bh.BH_BF16)]
         for stars, N, dtype in calls:
             dst = torch.from_numpy(stars).cuda()
             rec = torch.empty((bh.bh_cubemap_records(N), 4), dtype=torch.int16, device="cuda")
@@ -43,7 +51,7 @@ def test_noalloc_cubemap_matches_allocating_build_twice():
             got = rec.cpu().numpy().view(np.uint16)
             ref = reference_records(ctx, stars, N, dtype)
             # the cube map is integer/bit work: the tolerance is exact equality
-            assert np.array_equal(got, ref)
+            assert np.array_equal(got, ref), (len(stars), N, dtype)
     finally:
         bh.bh_destroy(ctx)
 
