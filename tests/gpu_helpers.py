@@ -41,12 +41,13 @@ def dilate(m: np.ndarray, r: int = 1) -> np.ndarray:
     return out
 
 
-def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndarray:
-    """Pixels excluded from the comparison, from the oracle's values only:
-    within 1 px of a change of disc-hit count or of the capture state (disc
-    edges, shadow silhouette), and pixels whose mip-level or cube-face
-    decision lies within a small margin of its threshold (a discontinuity of
-    the method, where FP32 and FP64 may take either side)."""
+def mask_parts(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> dict:
+    """The groups of pixels excluded from the comparison, from the oracle's
+    values only: within 1 px of a change of disc-hit count or of the capture
+    state (disc edges, shadow silhouette: the mask the tolerance names), and
+    pixels whose mip-level or cube-face decision lies within a small margin of
+    its threshold, or whose footprint Jacobian is degenerate (discontinuities
+    of the method, where FP32 and FP64 may take either side)."""
     cap = ~np.isfinite(dbg[..., 2])
     hits = dbg[..., 3]
     edge = np.zeros(cap.shape, dtype=bool)
@@ -57,7 +58,6 @@ def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndar
         e[1:, :] |= a[1:, :] != a[:-1, :]
         e[:-1, :] |= a[1:, :] != a[:-1, :]
         edge |= e
-    m = dilate(edge, 1)
     lvl = dbg[..., 6]
     hm = dbg[..., 16]
     has = lvl >= 0
@@ -65,9 +65,39 @@ def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndar
     near_up = has & (ratio > 1 - level_margin) & (ratio <= 1)
     prev = np.where(has & (lvl > 0), 2 * hm / (8 * 2.0 ** np.maximum(lvl - 1, 0)), 0.0)
     near_dn = has & (lvl > 0) & (prev < 1 + level_margin)
-    near_face = has & (dbg[..., 17] < face_margin)
-    degenerate = has & (dbg[..., 18] < 1e-5)
-    return m | near_up | near_dn | near_face | degenerate
+    return {"edge": dilate(edge, 1), "level_margin": near_up | near_dn,
+            "face_margin": has & (dbg[..., 17] < face_margin),
+            "degenerate": has & (dbg[..., 18] < 1e-5)}
+
+
+def oracle_mask(dbg: np.ndarray, level_margin=0.02, face_margin=2e-3) -> np.ndarray:
+    """Union of mask_parts: the pixels excluded from the comparison."""
+    m = np.zeros(dbg.shape[:2], dtype=bool)
+    for v in mask_parts(dbg, level_margin, face_margin).values():
+        m |= v
+    return m
+
+
+# Bounds on the share of an image each excluded group may take: the mask
+# must stay a thin set (edges and decision thresholds), never a region.  A
+# +-2 % band around every mip-level threshold covers 2 x log2(1.02) = 5.7 %
+# of the pixels when log2 of the footprint is spread evenly over the image.
+MASK_BOUNDS = {"edge": 0.30, "level_margin": 0.08, "face_margin": 0.01, "degenerate": 0.01,
+               "ill_conditioned": 0.10}
+
+
+def mask_report(name: str, dbg: np.ndarray, orc: np.ndarray, cam: dict) -> dict:
+    """Share of the image in each excluded group (printed, and bounded by
+    MASK_BOUNDS)."""
+    parts = mask_parts(dbg)
+    rep = {k: float(v.mean()) for k, v in parts.items()}
+    rep["ill_conditioned"] = float((star_ill_conditioned(dbg, orc, cam) & ~oracle_mask(dbg)).mean())
+    print(f"MASK {name} {cam['width']}x{cam['height']}: " +
+          " ".join(f"{k}={v:.4f}" for k, v in rep.items()))
+    if cam["width"] * cam["height"] >= 4096:  # tiny test images are mostly edge
+        for k, v in rep.items():
+            assert v <= MASK_BOUNDS[k], (name, k, v)
+    return rep
 
 
 # FP32 places a beam's escape direction to a few float ulps of the angle,

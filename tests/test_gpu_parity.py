@@ -13,7 +13,8 @@ import pytest
 
 from paper_2010_08735_gb300 import synth
 from gpu_helpers import (HIT_U_REL, RGB_MAX_REL, RGB_MEAN_REL, TABLE_REL, image_error,
-                         ill_conditioned_ok, maybe_dump, oracle_mask, star_ill_conditioned)
+                         ill_conditioned_ok, mask_report, maybe_dump, oracle_mask,
+                         star_ill_conditioned)
 
 pytestmark = pytest.mark.gpu
 
@@ -118,10 +119,20 @@ def test_uploaded_tables_time_channel(ctx, orc_tables_t):
 
 
 def test_colour_tables_match_oracle(gpu_tables, orc_colour):
+    """C(xy, D) and the disc black-body table: both computed in FP64 on the
+    GPU and stored as FP32, so each value is the oracle's to within the FP32
+    rounding of its storage: 2^-24 relative, or, for the faint corners of C
+    below FP32's normal range (1.18e-38), that range's absolute spacing."""
     Cg, dg = bh.bh_tables_copy_colour(gpu_tables)
     Co, do = orc_colour
-    assert np.allclose(Cg[..., :3], Co, rtol=1e-5, atol=1e-30)
-    assert np.allclose(dg[:, :3], do, rtol=1e-5, atol=1e-4)
+    tiny = float(np.finfo(np.float32).tiny)
+    for name, g, o in (("C", Cg[..., :3], Co), ("disc", dg[:, :3], do)):
+        err = np.abs(g.astype(np.float64) - o)
+        bound = 2.0 ** -24 * np.abs(o) * (1 + 1e-6) + tiny
+        normal = np.abs(o) >= tiny
+        print(f"{name} table: max relative difference {(err[normal] / np.abs(o[normal])).max():.3e} "
+              f"over {normal.sum()} normal values, {(~normal).sum()} below FP32's normal range")
+        assert np.all(err <= bound), name
 
 
 def test_invalid_arguments(ctx, gpu_tables):
@@ -234,7 +245,9 @@ def check_stages(gd, od, mask):
         assert dd.max() < 1e-3, dd.max()
     # disc hits: same count and radius within 1e-3 relative
     same = ~mask & (gd[..., 3] == od[..., 3])
-    assert (~mask & (gd[..., 3] != od[..., 3])).sum() <= 0.001 * (~mask).sum()
+    nhit = (~mask & (gd[..., 3] != od[..., 3])).sum()
+    print(f"HITCOUNT differing on {nhit} of {(~mask).sum()} unmasked pixels")
+    assert nhit <= 0.001 * (~mask).sum()
     for k, ch in ((1, 4), (2, 5)):
         sel = same & (od[..., 3] >= k)
         if sel.any():
@@ -247,7 +260,8 @@ def check_stages(gd, od, mask):
         assert (gd[..., 7][has] != od[..., 7][has]).mean() < 1e-3
 
 
-def check_rgb(og, oo, od, mask, cam):
+def check_rgb(og, oo, od, mask, cam, name="render"):
+    mask_report(name, od, oo, cam)
     ill = star_ill_conditioned(od, oo, cam)
     mean, mx, rel = image_error(og, oo, mask | ill)
     assert mean <= RGB_MEAN_REL and mx <= RGB_MAX_REL, (mean, mx)
@@ -262,7 +276,7 @@ def test_render_static_256(ctx, orc, gpu_tables, static_scene):
                                           name="static_256")
     assert mask.mean() < 0.2
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask, wk["camera"])
+    check_rgb(og, oo, od, mask, wk["camera"], "static_256")
 
 
 def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_scene):
@@ -271,7 +285,7 @@ def test_render_uploaded_tables_static_256(ctx, orc, uploaded_tables, static_sce
     og, gd, oo, od, mask = compare_render(orc, ctx, uploaded_tables, cube, scene, wk["camera"],
                                           wk["disc"], name="static_256_uploaded")
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask, wk["camera"])
+    check_rgb(og, oo, od, mask, wk["camera"], "static_256_uploaded")
 
 
 ANIM_CAMS = [
@@ -311,7 +325,7 @@ def test_render_animated_disc(ctx, orc, orc_tables_t, orc_colour, gpu_tables, st
     assert n > 0
     dens = od[..., 25][od[..., 3] >= 1]
     assert dens.std() > 0.1 and (dens < 1).mean() > 0.5  # the density varies, mostly unclamped
-    check_rgb(og, oo, od, mask, cam)
+    check_rgb(og, oo, od, mask, cam, "animated")
 
 
 def test_disc_particles_invalid(ctx):
@@ -382,7 +396,7 @@ def test_render_configs_small(ctx, orc, gpu_tables, static_scene, cam):
     og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, cam, disc,
                                           name=f"small_{cam['width']}x{cam['height']}_r{cam['r']}")
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask, cam)
+    check_rgb(og, oo, od, mask, cam, "small")
 
 
 def test_star_centroids_sparse_field(ctx, orc, orc_tables, orc_colour, gpu_tables):
@@ -579,13 +593,16 @@ def test_full_size_sampled_rows(ctx, orc, orc_tables, orc_colour, gpu_tables, na
     cube = bh.bh_build_star_cubemap(ctx, st, N, dt)
     try:
         rec = orc.build_cubemap(st, N, dt)
+        # the full cube map of the workload (1M stars at 2048^2 FP16, 4M at
+        # 4096^2 BF16), record for record: integer work, exact equality
+        assert np.array_equal(bh.bh_cubemap_copy_out(cube, N), rec)
         scene = orc_scene(orc, orc_tables, orc_colour, rec, N, dt)
         og, gd, oo, od, mask = compare_render(orc, ctx, gpu_tables, cube, scene, wk["camera"],
                                               wk["disc"], y0=rows[0], y1=rows[1], name=name)
     finally:
         bh.bh_cubemap_free(cube)
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask, wk["camera"])
+    check_rgb(og, oo, od, mask, wk["camera"], name)
 
 
 @pytest.mark.parametrize("name", ["orbit_1080p", "infall_4k"])
@@ -618,6 +635,39 @@ def test_timed_kernel_equals_checked_render_full_size(gpu_tables, name):
         bh.bh_destroy(c2)
 
 
+def test_timed_animated_kernel_equals_checked_render_full_size(gpu_tables):
+    """The animated-disc kernel the benchmark times (16 linear particles,
+    Appendix B) renders every pixel of the 1080p frame exactly as the checked
+    debug render -- which test_render_animated_disc compares with the oracle --
+    at two frame times."""
+    wk = synth.WORKLOADS["orbit_1080p"]
+    cam, disc0 = wk["camera"], wk["disc"]
+    W, H = cam["width"], cam["height"]
+    c2 = bh.bh_create(0, 0)
+    cube = bh.bh_build_star_cubemap(c2, synth.stars(wk["n_stars"], wk["star_seed"]), wk["cube_n"], bh.BH_F16)
+    ph = bh.bh_disc_particles_create(c2, synth.disc_particles(16, 5, disc0["r_in"], disc0["r_out"]))
+    try:
+        sh = bh.make_shading(1.0, 0.01)
+        plain = torch.zeros((H, W, 4), device="cuda")
+        bh.bh_autotune_batch(c2, gpu_tables, cube, [cam], disc0, sh, [plain])
+        dbg_out = torch.zeros_like(plain)
+        dbg = torch.zeros((H, W, bh.NDBG), device="cuda")
+        for t in (3.0, 1234.5):
+            disc = dict(disc0, particles_handle=ph, time=t)
+            plain.zero_()
+            bh.bh_render(c2, gpu_tables, cube, cam, disc, sh, plain)
+            bh.bh_render_debug(c2, gpu_tables, cube, cam, disc, sh, dbg_out, dbg)
+            torch.cuda.synchronize()
+            assert bh.bh_check_status(c2) == bh.BH_OK
+            assert torch.equal(plain, dbg_out), t
+            dens = dbg[..., 18][dbg[..., 3] >= 1]
+            assert dens.numel() > 0 and float(dens.std()) > 0.05  # particles really shade the frame
+    finally:
+        bh.bh_disc_particles_free(ph)
+        bh.bh_cubemap_free(cube)
+        bh.bh_destroy(c2)
+
+
 @pytest.mark.parametrize("cam", [synth.WORKLOADS["static_256"]["camera"],
                                  synth.camera(3.2, 89.0, v=(-0.9, 0.0, 0.0), width=96, height=54)])
 def test_render_f16_tables(ctx, orc, orc_tables, orc_colour, static_scene, cam):
@@ -637,7 +687,7 @@ def test_render_f16_tables(ctx, orc, orc_tables, orc_colour, static_scene, cam):
     finally:
         bh.bh_tables_free(t)
     check_stages(gd, od, mask)
-    check_rgb(og, oo, od, mask, cam)
+    check_rgb(og, oo, od, mask, cam, "f16_tables")
 
 
 def test_table_storage_precision_report(ctx, orc, orc_tables, orc_colour, static_scene):
