@@ -77,6 +77,70 @@ class Orbit(C.Structure):
 _D = C.POINTER(C.c_double)
 
 
+LIB_COUNT = HERE / "liboracle_count.so"
+_lib_count = None
+COUNT_CLASSES = ("add", "mul", "div", "sqrt", "transcendental", "compare", "other",
+                 "fetch_D", "fetch_U", "fetch_C", "fetch_disc", "fetch_cube")
+
+
+def build_count(force: bool = False) -> Path:
+    """Compile the counting build (op_count.cpp: this oracle as C++ with
+    counting doubles) into ``oracle/liboracle_count.so``."""
+    deps = [SRC, HERE / "op_count.cpp", HERE / "op_count.hpp"]
+    if force or not LIB_COUNT.exists() or any(LIB_COUNT.stat().st_mtime < d.stat().st_mtime for d in deps):
+        tmp = LIB_COUNT.with_suffix(f".so.tmp{os.getpid()}")
+        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall",
+               "-o", str(tmp), str(HERE / "op_count.cpp"), "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True, cwd=str(HERE))
+        os.replace(tmp, LIB_COUNT)
+    return LIB_COUNT
+
+
+def lib_count():
+    global _lib_count
+    if _lib_count is None:
+        build_count()
+        L = C.CDLL(str(LIB_COUNT))
+        L.orc_render.restype = C.c_int
+        L.orc_render.argtypes = [C.POINTER(Camera), C.POINTER(Disc), C.c_double, C.c_double,
+                                 C.POINTER(Scene), C.c_int, C.c_int, C.c_int, C.c_int,
+                                 _D, _D, C.POINTER(C.c_longlong)]
+        L.orc_count_reset.restype = None
+        L.orc_count_reset.argtypes = [C.c_longlong]
+        L.orc_count_read.restype = None
+        L.orc_count_read.argtypes = [C.POINTER(C.c_longlong)]
+        _lib_count = L
+    return _lib_count
+
+
+def count_render(cam: dict, disc: dict, tables: "SceneTables", exposure_disc=1.0, exposure_stars=0.01,
+                 y0=0, y1=None, nthreads=None):
+    """The oracle's render of rows [y0, y1) in its counting build: returns
+    (rgba, counts), counts a dict of the per-pixel work tallied by class
+    (COUNT_CLASSES), the unique cube-map records read ("unique_cube_records")
+    and the unique occupied ones ("unique_cube_records_occupied")."""
+    L = lib_count()
+    c = make_camera(cam)
+    d = make_disc(disc)
+    y1 = cam["height"] if y1 is None else y1
+    out = np.zeros((y1 - y0, cam["width"], 4))
+    tex = C.c_longlong(0)
+    s = tables.scene()
+    nrec = cube_records(tables.cube_n) if tables.cube is not None else 0
+    L.orc_count_reset(nrec)
+    rc = L.orc_render(C.byref(c), C.byref(d), exposure_disc, exposure_stars, C.byref(s), y0, y1, -1,
+                      nthreads or (os.cpu_count() or 1), _dp(out), None, C.byref(tex))
+    if rc:
+        raise ValueError(f"orc_render (counting) failed ({rc})")
+    raw = (C.c_longlong * (len(COUNT_CLASSES) + 2))()
+    L.orc_count_read(raw)
+    counts = dict(zip(COUNT_CLASSES, raw[:len(COUNT_CLASSES)]))
+    counts["unique_cube_records"] = raw[len(COUNT_CLASSES)]
+    counts["unique_cube_records_occupied"] = raw[len(COUNT_CLASSES) + 1]
+    counts["pixels"] = (y1 - y0) * cam["width"]
+    return out, counts
+
+
 def lib():
     global _lib
     if _lib is None:

@@ -48,6 +48,18 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Counting hooks (no-ops here).  The counting build (op_count.cpp, test
+ * infrastructure) compiles this file as C++ with every double replaced by a
+ * counting double and defines these to tally the per-pixel work: operations
+ * by class, table texels read, and the cube-map records touched. */
+#ifndef ORC_COUNTING
+#define ORC_COUNT_PAUSE()
+#define ORC_COUNT_RESUME()
+#define ORC_COUNT_FLUSH()
+#define ORC_FETCH(cls, k)
+#define ORC_TOUCH(rec, occupied)
+#endif
+
 #define MU (4.0 / 27.0) /* max of u^2 (1-u) on [0,1], at the photon sphere u = 2/3 (Sec. 3.3.1) */
 #define PI 3.14159265358979323846
 
@@ -365,6 +377,7 @@ double orc_d_lookup(const double *D, int n, double e2, double u) {
     y = (sqrt(2.0 / 3.0) + (u >= 2.0 / 3.0 ? s : -s)) / (sqrt(2.0 / 3.0) + sqrt(1.0 / 3.0));
     xlo = n / 2; xhi = n - 1;
   }
+  ORC_FETCH(kFetchD, 4);
   return bilinear(D, n, n, x * (n - 1), y * (n - 1), xlo, xhi);
 }
 
@@ -373,6 +386,7 @@ double orc_u_lookup(const double *U, int ne, int nphi, double e2, double phi) {
   double e = sqrt(e2);
   double x = 1.0 / (1.0 + 6.0 * e2);
   double y = phi / 3.0 * (1.0 + 6.0 * e2 * e) / (1.0 + e2);
+  ORC_FETCH(kFetchU, 4);
   return bilinear(U, ne, nphi, x * (ne - 1), y * (nphi - 1), 0, ne - 1);
 }
 
@@ -532,6 +546,7 @@ static void disc_xyz(const double *tab, int n, double T, double *xyz) {
   int k0 = (int)floor(f);
   int k1 = k0 + 1 > n - 1 ? n - 1 : k0 + 1;
   double t = f - k0;
+  ORC_FETCH(kFetchDisc, 2);
   double Y = exp(lerp(tab[3 * k0], tab[3 * k1], t));
   xyz[0] = Y * lerp(tab[3 * k0 + 1], tab[3 * k1 + 1], t);
   xyz[1] = Y;
@@ -611,6 +626,7 @@ static void c_lookup(const double *C, int nx, int ny, int nd, double x, double y
     t[a] = f[a] - i0[a];
   }
   out[0] = out[1] = out[2] = 0.0;
+  ORC_FETCH(kFetchC, 8);
   for (int c = 0; c < 8; ++c) {
     int ii = (c & 1) ? i1[0] : i0[0], jj = (c & 2) ? i1[1] : i0[1], kk = (c & 4) ? i1[2] : i0[2];
     double w = ((c & 1) ? t[0] : 1.0 - t[0]) * ((c & 2) ? t[1] : 1.0 - t[1]) *
@@ -1165,12 +1181,14 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
   int nl = orc_cube_levels(N);
   {
     /* decision margins, for masking comparisons at discontinuities */
+    ORC_COUNT_PAUSE();
     double a[3] = {fabs(d[0]), fabs(d[1]), fabs(d[2])}, mx = a[0], sd = -1.0;
     for (int k = 1; k < 3; ++k) if (a[k] > mx) mx = a[k];
     for (int k = 0; k < 3; ++k) if (a[k] < mx && a[k] > sd) sd = a[k];
     int nmax = (a[0] == mx) + (a[1] == mx) + (a[2] == mx);
     dbg[16] = hm;
     dbg[17] = nmax > 1 ? 0.0 : 1.0 - sd / mx;
+    ORC_COUNT_RESUME();
   }
   int L = 0;
   if (J->force_level >= 0) L = J->force_level;
@@ -1183,7 +1201,9 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
   double a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
   double det = a11 * a22 - a12 * a21;
   /* reading C18: skip a degenerate footprint */
+  ORC_COUNT_PAUSE();
   dbg[18] = fabs(det) / sqrt((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22));
+  ORC_COUNT_RESUME();
   if (!(fabs(det) > 1e-6 * sqrt((a11 * a11 + a21 * a21) * (a12 * a12 + a22 * a22)))) return;
   double i11 = a22 / det, i12 = -a12 / det, i21 = -a21 / det, i22 = a11 / det;
   int i0 = (int)floor(cS - hsL), i1 = (int)floor(cS + hsL);
@@ -1200,8 +1220,13 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
     for (int ii = i0; ii <= i1; ++ii) {
       ++cnt;
       const uint16_t *r = rec + ((long long)jj * NL + ii) * 4;
+      ORC_FETCH(kFetchCube, 1);
+      ORC_TOUCH(orc_cube_level_offset(N, L) + (long long)face * NL * NL + (long long)jj * NL + ii,
+                (r[0] | r[1] | r[2]) != 0);
+      ORC_COUNT_PAUSE(); /* decoding a record is bit work, not arithmetic */
       double X = orc_decode16(r[0], sc->cube_dtype), Y = orc_decode16(r[1], sc->cube_dtype),
              Z = orc_decode16(r[2], sc->cube_dtype);
+      ORC_COUNT_RESUME();
       if (X + Y + Z <= 0.0) continue;
       double ps = ((r[3] & 255) + 0.5) / 256.0, pt = ((r[3] >> 8) + 0.5) / 256.0;
       double ds = ii + ps - cS, dt = jj + pt - cT;
@@ -1210,12 +1235,16 @@ static void star_gather(render_job *J, const pix *P, const pix *Pw0, const pix *
       if (fw <= 0.0 || fh <= 0.0) continue;
       double wt = fw * fh * lscale;
       xyz[0] += wt * X; xyz[1] += wt * Y; xyz[2] += wt * Z;
+      ORC_COUNT_PAUSE();
       ysum += wt * Y;
       gw += (w > 0.0 ? 1.0 : -1.0) * fh * lscale * Y; /* d/d(shift in w) of the Y sum */
       gh += (h > 0.0 ? 1.0 : -1.0) * fw * lscale * Y;
+      ORC_COUNT_RESUME();
     }
+  ORC_COUNT_PAUSE();
   dbg[15] = (double)cnt;
   dbg[19] = ysum > 0.0 ? sqrt(gw * gw + gh * gh) / ysum : 0.0;
+  ORC_COUNT_RESUME();
   *texels += cnt;
 }
 
@@ -1241,11 +1270,14 @@ static void render_pixel(render_job *J, int i, int j, pix *quad[2][2], double *o
   double e = sqrt(P->tr[6]);
   for (int h = 0; h < (int)P->tr[1]; ++h) {
     double up = P->tr[2 + 2 * h];
-    /* the hit point: at angle psi from e_x' towards e_y' in the ray plane */
+    /* the hit point: at angle psi from e_x' towards e_y' in the ray plane
+     * (its azimuth is needed only by the animated disc) */
+    double rho = J->disc->density, hphi = 0.0;
+    if (J->disc->n_particles <= 0) ORC_COUNT_PAUSE();
     double psi = P->tr[3 + 2 * h], hd[3];
     for (int k = 0; k < 3; ++k) hd[k] = cos(psi) * J->F.rhat[k] + sin(psi) * P->b.ey[k];
-    double hphi = atan2(hd[1], hd[0]);
-    double rho = J->disc->density;
+    hphi = atan2(hd[1], hd[0]);
+    if (J->disc->n_particles <= 0) ORC_COUNT_RESUME();
     if (J->disc->n_particles > 0) /* animated disc: emitted at the retarded time (App. B) */
       rho = orc_disc_density(J->disc->particles, J->disc->n_particles, J->disc->density,
                              J->disc->time - P->tr[8 + h], 1.0 / up, hphi);
@@ -1278,10 +1310,12 @@ static void render_pixel(render_job *J, int i, int j, pix *quad[2][2], double *o
       /* bound on the change of each linear-RGB channel per screen pixel of
        * footprint shift: |d sum/d shift| / sum (channel 19) times the star
        * light seen through |M| (the XYZ -> RGB matrix mixes signs) */
+      ORC_COUNT_PAUSE();
       for (int c = 0; c < 3; ++c)
         d[20 + c] = d[19] * trans * s *
                     (fabs(J->rgbm[c * 3 + 0] * cc[0]) + fabs(J->rgbm[c * 3 + 1] * cc[1]) +
                      fabs(J->rgbm[c * 3 + 2] * cc[2]));
+      ORC_COUNT_RESUME();
     }
   } else {
     d[6] = -1; d[7] = -1;
@@ -1322,6 +1356,7 @@ static void *render_worker(void *argp) {
   }
   free(buf);
   J->texels[w->tid] = texels;
+  ORC_COUNT_FLUSH();
   return NULL;
 }
 
@@ -1348,11 +1383,13 @@ int orc_render(const orc_camera *cam, const orc_disc *disc, double exposure_disc
   J.cam = cam; J.disc = disc; J.exposure_disc = exposure_disc; J.exposure_stars = exposure_stars;
   J.sc = sc; J.y0 = y0; J.y1 = y1; J.force_level = force_level; J.nthreads = nthreads;
   J.out = out; J.dbg = dbg;
+  ORC_COUNT_PAUSE(); /* per-frame constants: not per-pixel work */
   camera_frame(cam, &J.F);
   orc_xyz_to_rgb_matrix(J.rgbm);
   double yp[3];
   disc_xyz(sc->disc_ln, sc->disc_n, disc->t_peak, yp);
   J.y_peak = yp[1] > 0.0 ? yp[1] : 1.0;
+  ORC_COUNT_RESUME();
   pthread_t th[64];
   worker_arg args[64];
   for (int t = 0; t < nthreads; ++t) {
