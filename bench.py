@@ -34,13 +34,10 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "1080p frames/s"
 WORKLOAD = "orbit_1080p"
-# FP32 work per unit, counted from the render kernel source (FMA = 2 flops):
-# beam set-up + TRACERAY + footprint + colour lookup + store per pixel, the
-# tent-filter inner loop per visited texel, disc shading per hit.
-FLOP_PER_PIXEL = 420
-FLOP_PER_TEXEL = 26
-FLOP_PER_HIT = 60
-FP32_LANES_PER_SM = 128
+# The algorithmic work of a frame of each workload, tallied by the oracle's
+# counting build (tests/golden/make_work_counts.py): arithmetic by class,
+# texels read and the unique cube-map records a frame touches.
+WORK_COUNTS = ROOT / "tests" / "golden" / "work_counts.json"
 
 
 def max_over_ranks(value: float, device, ws: int) -> float:
@@ -141,6 +138,50 @@ def render_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+def work_counts(name):
+    return json.loads(WORK_COUNTS.read_text())[name]
+
+
+def roofline(name, ms_per_frame, rates, sm_mhz, hbm_gbs, traffic=None):
+    """Roofline of the render kernel on one frame of workload `name`: the
+    slowest of three legs, each the method's own work (oracle counts) at the
+    measured peak of its unit:
+      fp32 -- add/sub + mul + div (one flop each, two per FMA lane-cycle) at the
+              measured FMA rate;
+      sfu  -- sqrt + elementary functions (at least one special-function
+              operation each) at the measured special-function rate;
+      hbm  -- 16 B per pixel stored + 8 B per unique cube-map record the frame
+              touches, at the measured copy bandwidth.
+    frac = (roofline time) / (measured time) = the largest leg's
+    achieved / peak."""
+    c = work_counts(name)
+    t = ms_per_frame / 1000.0
+    sms, hz = rates["sms"], sm_mhz * 1e6
+    flops = c["add"] + c["mul"] + c["div"]
+    sfu = c["sqrt"] + c["transcendental"]
+    nbytes = 16 * c["pixels"] + 8 * c["unique_cube_records"]
+    legs = {
+        "fp32": {"work_per_frame": flops, "unit": "TFLOP/s", "achieved": flops / t / 1e12,
+                 "peak": sms * rates["fp32_fma_per_sm_clk"] * 2 * hz / 1e12},
+        "sfu": {"work_per_frame": sfu, "unit": "Top/s", "achieved": sfu / t / 1e12,
+                "peak": sms * rates["mufu_per_sm_clk"] * hz / 1e12},
+        "hbm": {"work_per_frame": nbytes, "unit": "GB/s", "achieved": nbytes / t / 1e9, "peak": hbm_gbs},
+    }
+    for v in legs.values():
+        v["frac"] = v["achieved"] / v["peak"]
+        v["roofline_us"] = v["work_per_frame"] / (v["peak"] * (1e9 if v["unit"] == "GB/s" else 1e12)) * 1e6
+    top = max(legs, key=lambda k: legs[k]["frac"])
+    L = legs[top]
+    return {"bound": "hbm" if top == "hbm" else "alu", "leg": top, "achieved": L["achieved"],
+            "peak": L["peak"], "unit": L["unit"], "frac": L["frac"], "traffic": traffic,
+            "peak_note": (f"of measured: {sms} SMs x {rates['fp32_fma_per_sm_clk']:.1f} FMA / "
+                          f"{rates['mufu_per_sm_clk']:.1f} SFU results per SM per clock (the library's "
+                          f"microbenchmark) x {sm_mhz:.0f} MHz (median SM clock of the timed region); "
+                          f"HBM {hbm_gbs:.0f} GB/s (MEASURED_PEAKS.json)"),
+            "work_source": "tests/golden/work_counts.json (oracle counting build)",
+            "legs": legs, "measured_us": ms_per_frame * 1000.0}
+
+
 def workload_config(wk, ws=1):
     W, H = wk["camera"]["width"], wk["camera"]["height"]
     return {"workload": WORKLOAD, "width": W, "height": H, "camera": "r=6, theta=85deg, v=0.5c e_phi",
@@ -155,20 +196,29 @@ def orbit_camera(wk, step):
     return cam
 
 
-def cpu_baseline(wk, seconds=12.0, impl_line=False):
-    """The oracle, as it stands, on the host cores: full-resolution rows of the
-    same workload until about `seconds` of rendering, scaled to frames/s."""
+def oracle_scene(wk, tables64=False):
+    """The oracle's tables and star cube map for workload wk (FP32-stored
+    tables as the renderer reads them, or the FP64 tables themselves)."""
     import oracle
     from paper_2010_08735_gb300 import synth
-    t0 = time.perf_counter()
     D, U = oracle.tables_exact(512, 64, 32, 1e-3)
     Ct, dl = oracle.colour_table(), oracle.disc_colour_table()
-    st = synth.stars(wk["n_stars"], wk["star_seed"])
-    rec = oracle.build_cubemap(st, wk["cube_n"], 1 if wk["cube_dtype"] == "f16" else 2)
-    scene = oracle.SceneTables(D.astype(np.float32), U.astype(np.float32), Ct.astype(np.float32),
-                               dl.astype(np.float32), rec, wk["cube_n"],
-                               1 if wk["cube_dtype"] == "f16" else 2)
-    setup = time.perf_counter() - t0
+    dt = 1 if wk["cube_dtype"] == "f16" else 2
+    rec = oracle.build_cubemap(synth.stars(wk["n_stars"], wk["star_seed"]), wk["cube_n"], dt)
+    f = (lambda a: a) if tables64 else (lambda a: a.astype(np.float32))
+    return oracle.SceneTables(f(D), f(U), Ct.astype(np.float32), dl.astype(np.float32), rec, wk["cube_n"], dt), (D, U)
+
+
+def cpu_baseline(wk, seconds=12.0, scene=None, setup_s=0.0):
+    """The oracle, as it stands, on the host cores: full-resolution rows of the
+    same workload until about `seconds` of rendering, scaled to frames/s; and
+    on one core, 16 rows spread over the frame (two-row bands at eight
+    heights, so the shadow and the star field are both sampled)."""
+    import oracle
+    t0 = time.perf_counter()
+    if scene is None:
+        scene, _ = oracle_scene(wk)
+    setup = time.perf_counter() - t0 + setup_s
     cam = wk["camera"]
     H = cam["height"]
     cores = os.cpu_count() or 1
@@ -185,16 +235,100 @@ def cpu_baseline(wk, seconds=12.0, impl_line=False):
         rows += y1 - y0
         y += band
     fps = (rows / H) / tr
-    # one core: a 16-row band through the frame's centre
-    y0 = (H // 2 - 8) // 2 * 2
-    t = time.perf_counter()
-    oracle.render(cam, wk["disc"], scene, exposure_stars=0.01, y0=y0, y1=y0 + 16, nthreads=1)
-    fps1 = (16 / H) / (time.perf_counter() - t)
+    t1 = 0.0
+    for k in range(8):
+        y0 = (k * H // 8 + H // 16) // 2 * 2
+        t = time.perf_counter()
+        oracle.render(cam, wk["disc"], scene, exposure_stars=0.01, y0=y0, y1=y0 + 2, nthreads=1)
+        t1 += time.perf_counter() - t
+    fps1 = (16 / H) / t1
     return {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "one_core_value": fps1,
-            "sample": f"{rows} of {H} rows of the 1920x1080 frame ({rows * cam['width']} px), "
-                      f"FP64 C oracle with {cores} threads (one_core_value: 16 central rows on one thread); "
-                      f"oracle set-up {setup:.1f} s untimed"}
+            "sample": f"{rows} of {H} rows of the {cam['width']}x{H} frame ({rows * cam['width']} px), "
+                      f"FP64 C oracle with {cores} threads (one_core_value: 16 rows in eight 2-row bands spread "
+                      f"over the frame, one thread); oracle set-up {setup:.1f} s untimed"}
+
+
+def edge_mask(cap, hits):
+    """Pixels within 1 px of a change of capture state or disc-hit count (the
+    shadow silhouette and the disc edges), where no tolerance applies."""
+    e = np.zeros(cap.shape, dtype=bool)
+    for a in (cap, hits):
+        d = np.zeros(cap.shape, dtype=bool)
+        d[:, 1:] |= a[:, 1:] != a[:, :-1]
+        d[:, :-1] |= a[:, 1:] != a[:, :-1]
+        d[1:] |= a[1:] != a[:-1]
+        d[:-1] |= a[1:] != a[:-1]
+        e |= d
+    m = e.copy()
+    m[1:] |= e[:-1]
+    m[:-1] |= e[1:]
+    m2 = m.copy()
+    m2[:, 1:] |= m[:, :-1]
+    m2[:, :-1] |= m[:, 1:]
+    return m2
+
+
+def rel_error(img, ref, mask):
+    """Per-pixel relative linear-RGB error (denominator max(|ref|, 1e-4 max|ref|))
+    outside `mask`: mean, p99 and max."""
+    g = img[..., :3].astype(np.float64)
+    o = ref[..., :3].astype(np.float64)
+    floor = 1e-4 * max(np.abs(o).max(), 1e-30)
+    r = (np.abs(g - o) / np.maximum(np.abs(o), floor)).max(-1)[~mask]
+    return {"mean_rel": float(r.mean()), "p99_rel": float(np.percentile(r, 99)), "max_rel": float(r.max()),
+            "pixels": int(r.size), "masked": int(mask.sum())}
+
+
+def oracle_leg(wk, gpu_frames, seconds=12.0):
+    """Everything that runs the oracle (rank 0, one GPU): the CPU baseline, and
+    the error statement of the GPU's outputs against the FP64 oracle:
+    1080p frames rendered with FP32- and FP16-stored tables against the oracle
+    on the FP64 tables themselves (the tables' storage error), and the table
+    method against the table-free photon orbit on 1000 beams of the frame
+    (Sec. 4's accuracy statement, delta' in rad and u = r_s/r)."""
+    import oracle
+    from paper_2010_08735_gb300 import synth
+    t0 = time.perf_counter()
+    scene32, (D, U) = oracle_scene(wk)
+    cb = cpu_baseline(wk, seconds, scene=scene32, setup_s=time.perf_counter() - t0)
+    cam, disc = wk["camera"], wk["disc"]
+    exact = oracle.SceneTables(D, U, scene32.C, scene32.disc_ln, scene32.cube, scene32.cube_n,
+                               scene32.cube_dtype)
+    ref, dbg, _ = oracle.render(cam, disc, exact, exposure_stars=0.01, debug=True)
+    mask = edge_mask(~np.isfinite(dbg[..., 2]), dbg[..., 3])
+    del dbg
+    errors = {"workload": WORKLOAD, "reference": "FP64 oracle on the FP64 tables",
+              "mask": "pixels within 1 px of the shadow silhouette or a disc edge"}
+    for k, img in gpu_frames.items():
+        errors[k] = rel_error(img, ref, mask)
+    # table method vs the table-free 3D photon orbit (Sec. 4)
+    W, H = cam["width"], cam["height"]
+    th, ph = cam["theta"], cam["phi"]
+    er = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    rng = np.random.default_rng(11)
+    de, ue, nb = [], [], 0
+    while nb < 1000:
+        i, j = int(rng.integers(0, W)), int(rng.integers(0, H))
+        b = oracle.beam(cam, i + 0.5 - W / 2, H / 2 - j - 0.5)
+        tr = oracle.trace_ray(D, U, cam["r"], b["delta"], b["alpha"], 1 / disc["r_in"], 1 / disc["r_out"],
+                              b["alpha_valid"])
+        bf = oracle.bruteforce_ray(cam["r"] * er, b["dcart"], disc["r_in"], disc["r_out"])
+        nb += 1
+        if not bf["captured"] and not math.isinf(tr["delta_p"]):
+            dp = math.cos(tr["delta_p"]) * er + math.sin(tr["delta_p"]) * b["ey"]
+            de.append(math.acos(min(1.0, float(dp @ bf["dir"]))))
+        hits = [h[0] for h in tr["hits"]]
+        if len(hits) == len(bf["hits_u"][:2]):
+            ue += [abs(a - c) for a, c in zip(hits, bf["hits_u"][:2])]
+    de, ue = np.array(de), np.array(ue)
+    errors["table_method_vs_bruteforce"] = {
+        "beams": nb, "delta_prime_rad": {"p50": float(np.median(de)), "p99": float(np.percentile(de, 99)),
+                                         "max": float(de.max()), "n": int(de.size)},
+        "hit_u": {"p50": float(np.median(ue)), "p99": float(np.percentile(ue, 99)), "max": float(ue.max()),
+                  "n": int(ue.size)},
+        "paper_bound": 1e-3}
+    return cb, errors
 
 
 def run_reference(args):
@@ -203,7 +337,7 @@ def run_reference(args):
         return
     from paper_2010_08735_gb300 import synth
     wk = synth.WORKLOADS[WORKLOAD]
-    cb = cpu_baseline(wk, seconds=max(5.0, 2.0 * args.steps), impl_line=True)
+    cb = cpu_baseline(wk, seconds=max(5.0, 2.0 * args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "frames/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
@@ -213,6 +347,71 @@ def run_reference(args):
             "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def timed_frames(bh, ctx, tables, cube, wk, sh, out, flush, stream, steps, step0=0):
+    """Render `steps` frames of workload wk (camera moving along its orbit),
+    each after an L2 flush, each timed by CUDA events on its stream; returns
+    the per-frame milliseconds."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for s in range(steps):
+            flush.zero_()  # L2 flush between timed frames (256 MiB > 129 MB L2)
+            evs[s][0].record(stream)
+            bh.bh_render(ctx, tables, cube, orbit_camera(wk, step0 + s), wk["disc"], sh, out, stream)
+            evs[s][1].record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+
+def plain_wall_run(bh, ctx, tables, cube, wk, sh, out, stream, frames=2000):
+    """The plain form, measured like the served one: one bh_render per frame,
+    then a stream synchronisation; wall-clock latency per frame (launch to
+    completion seen by the host), no L2 flush (as in serving)."""
+    lat = []
+    for s in range(20):
+        bh.bh_render(ctx, tables, cube, orbit_camera(wk, s), wk["disc"], sh, out, stream)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for s in range(frames):
+        t = time.perf_counter()
+        bh.bh_render(ctx, tables, cube, orbit_camera(wk, s), wk["disc"], sh, out, stream)
+        stream.synchronize()
+        lat.append((time.perf_counter() - t) * 1000.0)
+    el = time.perf_counter() - t0
+    return {"frames_per_s": frames / el, "unit": "1080p frames/s", "frames": frames,
+            "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "l2": "not flushed (as served)"}
+
+
+def other_workload(bh, ctx, tables, name, sh, dev, stream, flush, rates, steps=200, warmup=5):
+    """Device-timed frames of another workload (its own star cube map), with
+    its roofline; returns (line, cube handle) -- the caller frees the cube."""
+    import torch
+    from paper_2010_08735_gb300 import synth
+    wk = synth.WORKLOADS[name]
+    W, H = wk["camera"]["width"], wk["camera"]["height"]
+    stars = torch.from_numpy(synth.stars(wk["n_stars"], wk["star_seed"])).to(dev)
+    cube = bh.bh_build_star_cubemap(ctx, stars, wk["cube_n"],
+                                    bh.BH_F16 if wk["cube_dtype"] == "f16" else bh.BH_BF16, stream)
+    del stars
+    out = torch.empty((H, W, 4), device=dev)
+    for s in range(warmup):
+        bh.bh_render(ctx, tables, cube, orbit_camera(wk, s), wk["disc"], sh, out, stream)
+    ms = timed_frames(bh, ctx, tables, cube, wk, sh, out, flush, stream, steps, warmup)
+    ms_frame = sum(ms) / len(ms)
+    line = {"workload": name, "width": W, "height": H, "stars": wk["n_stars"], "cube_face": wk["cube_n"],
+            "cube_dtype": wk["cube_dtype"], "frames": steps, "ms_per_frame": ms_frame,
+            "frames_per_s": 1000.0 / ms_frame, "mpix_per_s": W * H / ms_frame / 1000.0,
+            "l2": "flushed before each frame",
+            "roofline": roofline(name, ms_frame, rates, rates["sm_mhz_timed"],
+                                 (measured_peaks() or {}).get("hbm_gbs", 6800.0))}
+    return line, cube, out
 
 
 def run_ours(args):
@@ -234,6 +433,8 @@ def run_ours(args):
     ctx = bh.bh_create(local, 0)
     sh = bh.make_shading(1.0, 0.01)
     disc = wk["disc"]
+    # SM issue rates of this GPU (the library's microbenchmark; untimed)
+    rates = bh.bh_measure_issue_rates(local)
     # --- build (untimed for the frame metric; reported)
     t_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     with torch.cuda.stream(stream):
@@ -253,17 +454,8 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # launch shape for this frame size from the autotuner (untimed)
     tuned = bh.bh_autotune_batch(ctx, tables, cube, [cam0], disc, sh, [out])
-    # --- work counts for the roofline (one untimed debug render)
-    dbg = torch.empty((H, W, bh.NDBG), device=dev)
-    bh.bh_render_debug(ctx, tables, cube, cam0, disc, sh, out, dbg, stream)
-    stream.synchronize()
-    d = dbg.view(-1, bh.NDBG)
-    texels = float(d[:, 15].sum().item())
-    hits = float(d[:, 3].sum().item())
-    del dbg, d
-    flops_frame = W * H * FLOP_PER_PIXEL + texels * FLOP_PER_TEXEL + hits * FLOP_PER_HIT
 
-    # --- warm-up
+    # --- warm-up, then the timed frames
     for s in range(args.warmup):
         bh.bh_render(ctx, tables, cube, orbit_camera(wk, s), disc, sh, out, stream)
     stream.synchronize()
@@ -272,43 +464,55 @@ def run_ours(args):
     launches0 = bh.bh_kernel_launches(ctx)
     sampler = ClockSampler(local)
     sampler.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for s in range(args.steps):
-            flush.zero_()  # L2 flush between timed frames (256 MiB > 129 MB L2)
-            evs[s][0].record(stream)
-            bh.bh_render(ctx, tables, cube, orbit_camera(wk, args.warmup + s), disc, sh, out, stream)
-            evs[s][1].record(stream)
-    stream.synchronize()
+    frame_ms = timed_frames(bh, ctx, tables, cube, wk, sh, out, flush, stream, args.steps, args.warmup)
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
     clocks = sampler.stop()
     launches = bh.bh_kernel_launches(ctx) - launches0
-    frame_ms = [a.elapsed_time(b) for a, b in evs]
     t_dev = max_over_ranks(sum(frame_ms) / 1000.0, dev, ws)
     ms_per_step = 1000.0 * t_dev / args.steps
     fps = replica_throughput(args.steps, ws, t_dev)
+    rates["sm_mhz_timed"] = (clocks or {}).get("sm_mhz") or rates["sm_mhz"]
+    hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    rl = roofline(WORKLOAD, ms_per_step, rates, rates["sm_mhz_timed"], hbm, render_traffic())
+
+    if not args.extras:
+        # the timed frames alone (for profiling runs): no extra measurement legs
+        line = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(wk, ws),
+                "roofline": rl, "gpu_launches": int(launches), "clocks": clocks, "extras": False}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        bh.bh_cubemap_free(cube)
+        bh.bh_tables_free(tables)
+        bh.bh_destroy(ctx)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     # --- end to end through the C ABI with host buffers (D2H of every frame)
     host = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
-    for s in range(2):
+    for s in range(3):
         bh.bh_render_to_host(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
-    e2e_steps = max(5, min(200, args.steps // 2))
+    e2e_steps = max(200, min(1000, args.steps // 4))
     t = time.perf_counter()
     for s in range(e2e_steps):
         bh.bh_render_to_host(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
     e2e_t = time.perf_counter() - t
     e2e_fps = ws * e2e_steps / e2e_t
 
-    # --- served (continuous batching) and batched forms on the same frames
-    served = serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=max(32, args.steps))
+    # --- plain and served forms on equal terms: host wall clock per frame,
+    # 2000 frames each, the same cameras, no L2 flush on either side
+    plain = plain_wall_run(bh, ctx, tables, cube, wk, sh, out, stream, frames=2000)
+    served = serve_run(bh, ctx, tables, cube, wk, sh, dev, frames=2000)
+    served["served_over_plain"] = served["frames_per_s"] / plain["frames_per_s"]
     batched = batch_run(bh, ctx, tables, cube, sh, dev)
     orbits = orbit_run(bh, ctx, tables, cube, sh, dev)
     animated = animated_run(bh, ctx, tables, cube, wk, sh, out, flush, stream)
-    served_orbits = serve_orbits_run(bh, ctx, tables, cube, wk, sh, dev, frames=max(32, min(args.steps, 2000)))
+    served_orbits = serve_orbits_run(bh, ctx, tables, cube, wk, sh, dev, frames=2000)
     served_mixed = serve_workload(bh, dev, tables, cube, sh) if args.serve_workload else None
     if served_mixed is not None:
         # the largest per-viewer request rate whose p99 latency stays within two
@@ -322,11 +526,47 @@ def run_ours(args):
         served_mixed["rate_sweep"] = sweep
         served_mixed["max_rate_hz_p99_within_2_frames"] = max(ok) if ok else None
 
-    peaks = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = (clocks or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = flops_frame / (ms_per_step / 1000.0) / 1e12
+    # --- the other workloads, device-timed with their rooflines; the 4K
+    # frame's BF16 cube-map storage error (against the same frame on an FP16
+    # cube map, whose rounding is 8x finer)
+    others = {}
+    line256, cube256, _ = other_workload(bh, ctx, tables, "static_256", sh, dev, stream, flush, rates)
+    bh.bh_cubemap_free(cube256)
+    others["static_256"] = line256
+    line4k, cube4k, out4k = other_workload(bh, ctx, tables, "infall_4k", sh, dev, stream, flush, rates)
+    wk4 = synth.WORKLOADS["infall_4k"]
+    cam4 = wk4["camera"]
+    stars4 = torch.from_numpy(synth.stars(wk4["n_stars"], wk4["star_seed"])).to(dev)
+    cube4k16 = bh.bh_build_star_cubemap(ctx, stars4, wk4["cube_n"], bh.BH_F16, stream)
+    del stars4
+    dbg4 = torch.empty((cam4["height"], cam4["width"], bh.NDBG), device=dev)
+    bh.bh_render_debug(ctx, tables, cube4k, cam4, wk4["disc"], sh, out4k, dbg4, stream)
+    stream.synchronize()
+    cap4 = torch.isinf(dbg4[..., 2]).cpu().numpy()
+    hits4 = dbg4[..., 3].cpu().numpy()
+    del dbg4
+    img_bf16 = out4k.cpu().numpy()
+    bh.bh_render(ctx, tables, cube4k16, cam4, wk4["disc"], sh, out4k, stream)
+    stream.synchronize()
+    img_f16 = out4k.cpu().numpy()
+    bh.bh_cubemap_free(cube4k)
+    bh.bh_cubemap_free(cube4k16)
+    del out4k
+    line4k["bf16_cube_storage_error"] = dict(rel_error(img_bf16, img_f16, edge_mask(cap4, hits4)),
+                                             reference="the same 4K frame on an FP16 cube map of the same stars")
+    del img_bf16, img_f16
+    others["infall_4k"] = line4k
+
+    # --- GPU frames for the error statement: FP32- and FP16-stored tables
+    bh.bh_render(ctx, tables, cube, cam0, disc, sh, out, stream)
+    stream.synchronize()
+    frames = {"tables_f32": out.cpu().numpy()}
+    t16 = bh.bh_precompute_tables(ctx, 512, 64, 32, bh.BH_F16, stream)
+    bh.bh_render(ctx, t16, cube, cam0, disc, sh, out, stream)
+    stream.synchronize()
+    frames["tables_f16"] = out.cpu().numpy()
+    bh.bh_tables_free(t16)
+
     line = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -334,22 +574,20 @@ def run_ours(args):
         "config": workload_config(wk, ws),
         "mpix_per_s": fps * W * H / 1e6,
         "autotune_choice": tuned,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": render_traffic(),
-                     "peak_note": f"FP32 issue: {props.multi_processor_count} SMs x 128 lanes x 2 x {sm_max:.0f} MHz",
-                     "flops_per_frame": flops_frame, "texels_per_pixel": texels / (W * H)},
+        "roofline": rl,
+        "issue_rates": rates,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 200,
-                "d2h_bytes_per_step": W * H * 16},
+                "d2h_bytes_per_step": W * H * 16, "frames": e2e_steps},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "precompute_ms": {"tables_D_U_colour": precompute_ms, "cubemap_1M_stars": cubemap_ms},
-        "served": served, "served_orbits": served_orbits, "batched": batched, "orbits": orbits,
-        "animated_disc": animated,
-        "served_mixed": served_mixed,
+        "plain_wall": plain, "served": served, "served_orbits": served_orbits, "batched": batched,
+        "orbits": orbits, "animated_disc": animated, "served_mixed": served_mixed,
+        "other_workloads": others,
     }
     if rank == 0 and args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wk, seconds=12.0)
+        line["cpu_baseline"], line["errors"] = oracle_leg(wk, frames, seconds=12.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     bh.bh_cubemap_free(cube)
@@ -631,6 +869,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serve-workload", dest="serve_workload", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="after the timed frames, skip the other measurement legs (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
