@@ -414,6 +414,38 @@ def other_workload(bh, ctx, tables, name, sh, dev, stream, flush, rates, steps=2
     return line, cube, out
 
 
+def bloom_run(bh, ctx, out, W, H, fov_y, flush, stream, frames=400, levels=6):
+    """The lens-glare bloom (Sec. 3.4.3) of the 1080p frame, in place, each
+    call after an L2 flush, CUDA-event timed; HBM roofline on its algorithmic
+    bytes: the frame read and written once, each pyramid level written and
+    read twice (box level, blurred level)."""
+    import torch
+    w = bh.bh_bloom_weights(fov_y, H, levels)
+    buf = out.clone()
+    for _ in range(3):
+        bh.bh_bloom(ctx, buf, buf, W, H, w, stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+    with torch.cuda.stream(stream):
+        for s in range(frames):
+            flush.zero_()
+            evs[s][0].record(stream)
+            bh.bh_bloom(ctx, buf, buf, W, H, w, stream)
+            evs[s][1].record(stream)
+    stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / frames
+    texels, w_, h_ = 0, W, H
+    for _ in range(levels):
+        w_, h_ = (w_ + 1) // 2, (h_ + 1) // 2
+        texels += w_ * h_
+    nbytes = 16 * 2 * W * H + 16 * 4 * texels
+    hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    ach = nbytes / (ms / 1000.0) / 1e9
+    return {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms, "levels": levels, "launches_per_frame": 3 * levels + 1,
+            "weights": [float(x) for x in w],
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "bytes_per_frame": nbytes}}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -512,6 +544,7 @@ def run_ours(args):
     batched = batch_run(bh, ctx, tables, cube, sh, dev)
     orbits = orbit_run(bh, ctx, tables, cube, sh, dev)
     animated = animated_run(bh, ctx, tables, cube, wk, sh, out, flush, stream)
+    bloom = bloom_run(bh, ctx, out, W, H, cam0["fov_y"], flush, stream)
     served_orbits = serve_orbits_run(bh, ctx, tables, cube, wk, sh, dev, frames=2000)
     served_mixed = serve_workload(bh, dev, tables, cube, sh) if args.serve_workload else None
     if served_mixed is not None:
@@ -583,7 +616,7 @@ def run_ours(args):
         "wall_s_timed_region": wall,
         "precompute_ms": {"tables_D_U_colour": precompute_ms, "cubemap_1M_stars": cubemap_ms},
         "plain_wall": plain, "served": served, "served_orbits": served_orbits, "batched": batched,
-        "orbits": orbits, "animated_disc": animated, "served_mixed": served_mixed,
+        "orbits": orbits, "animated_disc": animated, "served_mixed": served_mixed, "bloom": bloom,
         "other_workloads": others,
     }
     if rank == 0 and args.cpu_baseline:

@@ -313,6 +313,34 @@ bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubem
                             const bh_shading *shading, float *const *outs, int *chosen);
 
 /* ------------------------------------------------------------------------ */
+/* Lens glare (Sec. 3.4.3)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Weights of the bloom's levels for a camera of vertical field of view fov_y
+ * (radians) and `height` pixels: weights[k] (k = 0..levels, levels <= 10) is
+ * the share of the photopic point spread function of Spencer et al. (1995),
+ *   P(theta) = 0.384 f0 + 0.478 f1 + 0.138 f2 (theta in degrees),
+ *   f0 = 2.61e6 exp(-(theta/0.02)^2), f1 = 20.91/(theta+0.02)^3,
+ *   f2 = 72.37/(theta+0.02)^2,
+ * falling between radii 2^(k-1/2) and 2^(k+1/2) pixels (k = 0: below
+ * 2^(1/2)), out of its energy below 2^(levels+1/2) pixels (pixel angle =
+ * fov_y / height).  The weights sum to 1.  Host only. */
+bh_status bh_bloom_weights(double fov_y, int height, int levels, double *weights);
+
+/* Bloom of a linear-RGB frame before tone mapping (Sec. 3.4.3: small filter
+ * kernels on mipmaps of the image approximating the PSF above).  in_device,
+ * out_device: width*height float4 (RGB, A = 1), 16-byte aligned; they may be
+ * the same buffer.  D_0 = in; D_k = 2x2 box average of D_{k-1} (sizes rounded
+ * up, indices clamped); B_k = D_k blurred by a separable 7-tap Gaussian of unit
+ * standard deviation (clamped); out = weights[0] in + sum_k weights[k]
+ * bilinear(B_k) at the pixel centre (clamped), k = 1..levels (<= 10).  The
+ * pyramid lives in context-owned scratch (allocated on first use, grown as
+ * needed), so bloom calls of one context must not overlap on the GPU
+ * (enqueue them on one stream).  Enqueued on `stream`. */
+bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_device, int width, int height,
+                   int levels, const double *weights, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Free-fall camera orbits (Appendix C), resident on the device               */
 /* ------------------------------------------------------------------------ */
 

@@ -113,6 +113,8 @@ def lib():
             "bh_serve_flush": [_vp],
             "bh_check_status": [_vp, _vp],
             "bh_measure_issue_rates": [C.c_int, P(C.c_double)],
+            "bh_bloom_weights": [C.c_double, C.c_int, C.c_int, P(C.c_double)],
+            "bh_bloom": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, P(C.c_double), _vp],
             "bh_inject_fault": [_vp, C.c_int],
         }
         for name, args in sig.items():
@@ -228,6 +230,20 @@ BH_FAULT_TABLE_WAIT = 1
 def bh_check_status(ctx: int, stream=None) -> int:
     """BH_OK, or raises BhError (BH_ERR_TIMEOUT / BH_ERR_DEVICE_STATUS)."""
     return _check(lib().bh_check_status(ctx, _stream(stream)))
+
+
+def bh_bloom_weights(fov_y: float, height: int, levels: int) -> np.ndarray:
+    """Per-level weights of the bloom (share of the PSF's energy per octave of radius)."""
+    w = np.zeros(levels + 1)
+    _check(lib().bh_bloom_weights(fov_y, height, levels, w.ctypes.data_as(C.POINTER(C.c_double))))
+    return w
+
+
+def bh_bloom(ctx, inp, out, width: int, height: int, weights, stream=None) -> None:
+    """Bloom of a (height, width, 4) float32 CUDA frame into `out` (may be `inp`)."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    _check(lib().bh_bloom(ctx, _ptr(inp), _ptr(out), width, height, w.size - 1,
+                          w.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
 
 
 def bh_measure_issue_rates(device: int = 0) -> dict:

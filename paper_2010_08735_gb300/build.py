@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           "--expt-relaxed-constexpr", "-I", str(HERE.parent / "include")]
 SOURCES = {"bh_core.cu": [], "bh_cubemap.cu": ["-fmad=false"],
-           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false", "-fmad=false"], "bh_serve.cu": [], "bh_io.cu": [], "bh_peaks.cu": []}
+           "bh_render.cu": ["-prec-div=false", "-prec-sqrt=false", "-fmad=false"], "bh_serve.cu": [], "bh_io.cu": [], "bh_peaks.cu": [], "bh_bloom.cu": []}
 
 
 def nvcc() -> str:

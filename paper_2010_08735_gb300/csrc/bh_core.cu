@@ -523,6 +523,7 @@ extern "C" void bh_destroy(bh_ctx *c) {
   if (c->cam_host) cudaFreeHost(c->cam_host);
   if (c->cam_dev) cudaFree(c->cam_dev);
   if (c->frame_dev) cudaFree(c->frame_dev);
+  if (c->bloom_dev) cudaFree(c->bloom_dev);
   if (c->orb_outs_host) cudaFreeHost(c->orb_outs_host);
   if (c->orb_outs_dev) cudaFree(c->orb_outs_dev);
   if (c->orb_cams_dev) cudaFree(c->orb_cams_dev);

@@ -117,6 +117,8 @@ struct bh_ctx {
   int orb_cap = 0;
   float *frame_dev = nullptr;         // bh_render_to_host frame buffer
   size_t frame_cap = 0;
+  void *bloom_dev = nullptr;          // bh_bloom: mip pyramid scratch
+  size_t bloom_cap = 0;
   bh::RenderTuning tuning;
   bh::ServeState *serve = nullptr;
   int inject_table_wait = 0;          // bh_inject_fault: next render's table wait never completes
