@@ -10,7 +10,9 @@
 // with w_k the share of the PSF's energy in the annulus of radii
 // [2^(k-1/2), 2^(k+1/2)) pixels (w_0: radii below 2^(1/2)), normalised over
 // radii below 2^(K+1/2); pixel angle = fov_y / height.  The weights are
-// computed on the host from the PSF's closed-form annulus integrals.
+// computed on the host from the PSF's closed-form annulus integrals.  The
+// whole bloom is one cooperative launch: the levels are separated by a
+// bounded grid barrier (a timeout sets a status bit, never hangs).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,70 +34,164 @@ static double psf_energy(double a, double b) {
   return 0.384 * (e0(b) - e0(a)) + 0.478 * (e1(b) - e1(a)) + 0.138 * (e2(b) - e2(a));
 }
 
-__global__ void bloom_down_kernel(const float4 *src, int sw, int sh, float4 *dst, int dw, int dh) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= dw || y >= dh) return;
+// 7-tap Gaussian of unit standard deviation, normalised (taps at -3..3)
+__constant__ float cBloomTaps[4];
+
+constexpr int kBloomTile = 32;                      // output texels per tile side
+constexpr int kBloomHalo = 3;                       // blur radius
+constexpr int kBloomSpan = kBloomTile + 2 * kBloomHalo;
+constexpr int kBloomThreads = 256;
+constexpr size_t kBloomSmem = sizeof(float4) * (kBloomSpan * kBloomSpan + kBloomSpan * kBloomTile);
+
+struct BloomParams {
+  const float4 *in;
+  float4 *out;
+  float4 *D[kBloomMaxLevels + 1];  // box levels (D[0] = in)
+  float4 *B[kBloomMaxLevels + 1];  // blurred levels
+  int w[kBloomMaxLevels + 1], h[kBloomMaxLevels + 1];
+  float wt[kBloomMaxLevels + 1];
+  int n;
+  unsigned *bar;        // grid-barrier arrival counter (zero at launch)
+  unsigned *status;
+  unsigned long long wait_ns;
+};
+
+// Grid-wide barrier for a cooperative launch (every block resident): each
+// block arrives once per phase and waits, for a bounded time, until all have
+// arrived.  On expiry it sets a status bit and returns false (the caller
+// stops), so a barrier can never hang the GPU.
+__device__ bool grid_barrier(const BloomParams &P, unsigned phase) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(P.bar, 1u);
+    const unsigned target = gridDim.x * phase;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    ok = 1;
+    unsigned seen;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(seen) : "l"(P.bar) : "memory");
+      if (seen >= target) break;
+      __nanosleep(100);
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > P.wait_ns) {
+        atomicOr(P.status, kStatusBarrierTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Box level k at texel (x, y), indices clamped to level k, from level k-1.
+__device__ __forceinline__ float4 box_texel(const BloomParams &P, int k, int x, int y) {
+  x = min(max(x, 0), P.w[k] - 1);
+  y = min(max(y, 0), P.h[k] - 1);
+  const int sw = P.w[k - 1], sh = P.h[k - 1];
+  const float4 *src = P.D[k - 1];
   const int x0 = min(2 * x, sw - 1), x1 = min(2 * x + 1, sw - 1);
   const int y0 = min(2 * y, sh - 1), y1 = min(2 * y + 1, sh - 1);
   const float4 a = src[(size_t)y0 * sw + x0], b = src[(size_t)y0 * sw + x1];
   const float4 c = src[(size_t)y1 * sw + x0], d = src[(size_t)y1 * sw + x1];
-  dst[(size_t)y * dw + x] = make_float4(0.25f * ((a.x + b.x) + (c.x + d.x)), 0.25f * ((a.y + b.y) + (c.y + d.y)),
-                                        0.25f * ((a.z + b.z) + (c.z + d.z)), 1.f);
+  return make_float4(0.25f * ((a.x + b.x) + (c.x + d.x)), 0.25f * ((a.y + b.y) + (c.y + d.y)),
+                     0.25f * ((a.z + b.z) + (c.z + d.z)), 1.f);
 }
 
-// 7-tap Gaussian of unit standard deviation, normalised (taps at -3..3)
-__constant__ float cBloomTaps[4];
-
-// dir 0: along x, 1: along y
-__global__ void bloom_blur_kernel(const float4 *src, float4 *dst, int w, int h, int dir) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= w || y >= h) return;
-  float r = 0.f, g = 0.f, b = 0.f;
+// One launch for the whole bloom: for each level, every block takes 32x32
+// tiles, builds the box level over the tile and a 3-texel halo in shared
+// memory (storing the tile's own texels for the next level), blurs along x
+// then y there and stores the blurred tile; a grid barrier separates the
+// levels; then every pixel of the frame is composited.
+__global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams P) {
+  extern __shared__ float4 sb[];
+  float4 *sD = sb;                              // kBloomSpan x kBloomSpan box texels
+  float4 *sH = sb + kBloomSpan * kBloomSpan;    // kBloomSpan rows x kBloomTile: blurred along x
+  for (int k = 1; k <= P.n; ++k) {
+    const int w = P.w[k], h = P.h[k];
+    const int tx = (w + kBloomTile - 1) / kBloomTile, tiles = tx * ((h + kBloomTile - 1) / kBloomTile);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int x0 = (tile % tx) * kBloomTile, y0 = (tile / tx) * kBloomTile;
+      for (int i = threadIdx.x; i < kBloomSpan * kBloomSpan; i += blockDim.x) {
+        const int r = i / kBloomSpan, c = i - r * kBloomSpan;
+        const int x = x0 + c - kBloomHalo, y = y0 + r - kBloomHalo;
+        const float4 v = box_texel(P, k, x, y);
+        sD[i] = v;
+        if (r >= kBloomHalo && r < kBloomHalo + kBloomTile && c >= kBloomHalo && c < kBloomHalo + kBloomTile &&
+            x < w && y < h)
+          P.D[k][(size_t)y * w + x] = v;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < kBloomSpan * kBloomTile; i += blockDim.x) {
+        const int r = i / kBloomTile, c = i - r * kBloomTile;
+        // taps past the level's edge read the clamped texel (the halo holds it
+        // only where the level continues)
+        const int x = x0 + c;
+        float rr = 0.f, gg = 0.f, bb = 0.f;
 #pragma unroll
-  for (int t = -3; t <= 3; ++t) {
-    const int xx = dir == 0 ? min(max(x + t, 0), w - 1) : x;
-    const int yy = dir == 1 ? min(max(y + t, 0), h - 1) : y;
-    const float4 v = src[(size_t)yy * w + xx];
-    const float k = cBloomTaps[t < 0 ? -t : t];
-    r = fmaf(k, v.x, r);
-    g = fmaf(k, v.y, g);
-    b = fmaf(k, v.z, b);
+        for (int t = -3; t <= 3; ++t) {
+          const int xx = min(max(x + t, 0), w - 1) - x0 + kBloomHalo;
+          const float4 v = sD[r * kBloomSpan + xx];
+          const float kt = cBloomTaps[t < 0 ? -t : t];
+          rr = fmaf(kt, v.x, rr);
+          gg = fmaf(kt, v.y, gg);
+          bb = fmaf(kt, v.z, bb);
+        }
+        sH[i] = make_float4(rr, gg, bb, 1.f);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < kBloomTile * kBloomTile; i += blockDim.x) {
+        const int r = i / kBloomTile, c = i - r * kBloomTile;
+        const int x = x0 + c, y = y0 + r;
+        if (x >= w || y >= h) continue;
+        float rr = 0.f, gg = 0.f, bb = 0.f;
+#pragma unroll
+        for (int t = -3; t <= 3; ++t) {
+          const int yy = min(max(y + t, 0), h - 1) - y0 + kBloomHalo;
+          const float4 v = sH[yy * kBloomTile + c];
+          const float kt = cBloomTaps[t < 0 ? -t : t];
+          rr = fmaf(kt, v.x, rr);
+          gg = fmaf(kt, v.y, gg);
+          bb = fmaf(kt, v.z, bb);
+        }
+        P.B[k][(size_t)y * w + x] = make_float4(rr, gg, bb, 1.f);
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(P, (unsigned)k)) return;
   }
-  dst[(size_t)y * w + x] = make_float4(r, g, b, 1.f);
-}
-
-struct BloomLevels {
-  const float4 *lev[kBloomMaxLevels + 1];
-  int w[kBloomMaxLevels + 1], h[kBloomMaxLevels + 1];
-  float wt[kBloomMaxLevels + 1];
-  int n;
-};
-
-__global__ void bloom_composite_kernel(const float4 *in, float4 *out, int W, int H, const BloomLevels L) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= H) return;
-  const float4 c = in[(size_t)y * W + x];
-  float r = L.wt[0] * c.x, g = L.wt[0] * c.y, b = L.wt[0] * c.z;
-  for (int k = 1; k <= L.n; ++k) {
-    const float s = 1.f / (float)(1 << k);
-    const float u = fmaf((float)x + 0.5f, s, -0.5f), v = fmaf((float)y + 0.5f, s, -0.5f);
-    const float fu = floorf(u), fv = floorf(v);
-    const float tu = u - fu, tv = v - fv;
-    const int w = L.w[k], h = L.h[k];
-    const int i0 = min(max((int)fu, 0), w - 1), i1 = min(max((int)fu + 1, 0), w - 1);
-    const int j0 = min(max((int)fv, 0), h - 1), j1 = min(max((int)fv + 1, 0), h - 1);
-    const float4 *p = L.lev[k];
-    const float4 a = p[(size_t)j0 * w + i0], bb = p[(size_t)j0 * w + i1];
-    const float4 cc = p[(size_t)j1 * w + i0], d = p[(size_t)j1 * w + i1];
-    const float wk = L.wt[k];
-    const float lr = fmaf(tv, fmaf(tu, d.x - cc.x, cc.x) - fmaf(tu, bb.x - a.x, a.x), fmaf(tu, bb.x - a.x, a.x));
-    const float lg = fmaf(tv, fmaf(tu, d.y - cc.y, cc.y) - fmaf(tu, bb.y - a.y, a.y), fmaf(tu, bb.y - a.y, a.y));
-    const float lb = fmaf(tv, fmaf(tu, d.z - cc.z, cc.z) - fmaf(tu, bb.z - a.z, a.z), fmaf(tu, bb.z - a.z, a.z));
-    r = fmaf(wk, lr, r);
-    g = fmaf(wk, lg, g);
-    b = fmaf(wk, lb, b);
+  // composite at full resolution
+  const int W = P.w[0], H = P.h[0];
+  const long long npx = (long long)W * H;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(p / W), x = (int)(p - (long long)y * W);
+    const float4 c = P.in[p];
+    float r = P.wt[0] * c.x, g = P.wt[0] * c.y, b = P.wt[0] * c.z;
+    for (int k = 1; k <= P.n; ++k) {
+      const float s = 1.f / (float)(1 << k);
+      const float u = fmaf((float)x + 0.5f, s, -0.5f), v = fmaf((float)y + 0.5f, s, -0.5f);
+      const float fu = floorf(u), fv = floorf(v);
+      const float tu = u - fu, tv = v - fv;
+      const int w = P.w[k], h = P.h[k];
+      const int i0 = min(max((int)fu, 0), w - 1), i1 = min(max((int)fu + 1, 0), w - 1);
+      const int j0 = min(max((int)fv, 0), h - 1), j1 = min(max((int)fv + 1, 0), h - 1);
+      const float4 *q = P.B[k];
+      const float4 a = q[(size_t)j0 * w + i0], bb = q[(size_t)j0 * w + i1];
+      const float4 cc = q[(size_t)j1 * w + i0], d = q[(size_t)j1 * w + i1];
+      const float wk = P.wt[k];
+      const float lr = fmaf(tv, fmaf(tu, d.x - cc.x, cc.x) - fmaf(tu, bb.x - a.x, a.x), fmaf(tu, bb.x - a.x, a.x));
+      const float lg = fmaf(tv, fmaf(tu, d.y - cc.y, cc.y) - fmaf(tu, bb.y - a.y, a.y), fmaf(tu, bb.y - a.y, a.y));
+      const float lb = fmaf(tv, fmaf(tu, d.z - cc.z, cc.z) - fmaf(tu, bb.z - a.z, a.z), fmaf(tu, bb.z - a.z, a.z));
+      r = fmaf(wk, lr, r);
+      g = fmaf(wk, lg, g);
+      b = fmaf(wk, lb, b);
+    }
+    P.out[p] = make_float4(r, g, b, 1.f);
   }
-  out[(size_t)y * W + x] = make_float4(r, g, b, 1.f);
 }
 
 }  // namespace bh
@@ -130,18 +226,17 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
   }
   BH_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  // pyramid sizes and scratch: D_k and B_k per level, plus one blur temporary
+  // pyramid sizes and scratch: D_k and B_k per level
   int w[kBloomMaxLevels + 1], h[kBloomMaxLevels + 1];
   w[0] = width;
   h[0] = height;
-  size_t texels = 0, tmp = 0;
+  size_t texels = 0;
   for (int k = 1; k <= levels; ++k) {
     w[k] = (w[k - 1] + 1) / 2;
     h[k] = (h[k - 1] + 1) / 2;
     texels += 2 * (size_t)w[k] * h[k];
-    tmp = std::max(tmp, (size_t)w[k] * h[k]);
   }
-  const size_t need = (texels + tmp) * sizeof(float4);
+  const size_t need = std::max<size_t>(texels, 1) * sizeof(float4);
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (need > ctx->bloom_cap) {
     if (ctx->bloom_dev) {
@@ -153,7 +248,9 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
     BH_CUDA(cudaMalloc((void **)&ctx->bloom_dev, need));
     ctx->bloom_cap = need;
   }
+  if (!ctx->bloom_bar) BH_CUDA(cudaMalloc((void **)&ctx->bloom_bar, sizeof(unsigned)));
   static bool taps_ready[64] = {false};
+  static int coop_blocks[64] = {0};
   if (ctx->device < 64 && !taps_ready[ctx->device]) {
     double t[4], sum = 0.0;
     for (int i = 0; i < 4; ++i) {
@@ -163,34 +260,37 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
     float tf[4];
     for (int i = 0; i < 4; ++i) tf[i] = (float)(t[i] / sum);
     BH_CUDA(cudaMemcpyToSymbol(cBloomTaps, tf, sizeof tf));
+    int per_sm = 0;
+    BH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bloom_kernel, kBloomThreads, kBloomSmem));
+    coop_blocks[ctx->device] = std::max(1, std::min(per_sm, 4)) * ctx->sm_count;
     taps_ready[ctx->device] = true;
   }
-  BloomLevels L;
-  memset(&L, 0, sizeof L);
-  L.n = levels;
+  BloomParams P;
+  memset(&P, 0, sizeof P);
+  P.in = reinterpret_cast<const float4 *>(in_device);
+  P.out = reinterpret_cast<float4 *>(out_device);
+  P.n = levels;
+  float4 *cur = reinterpret_cast<float4 *>(ctx->bloom_dev);
   for (int k = 0; k <= levels; ++k) {
-    L.w[k] = w[k];
-    L.h[k] = h[k];
-    L.wt[k] = (float)weights[k];
+    P.w[k] = w[k];
+    P.h[k] = h[k];
+    P.wt[k] = (float)weights[k];
+    if (k == 0) {
+      P.D[0] = const_cast<float4 *>(P.in);
+    } else {
+      P.D[k] = cur;
+      P.B[k] = cur + (size_t)w[k] * h[k];
+      cur = P.B[k] + (size_t)w[k] * h[k];
+    }
   }
-  float4 *base = reinterpret_cast<float4 *>(ctx->bloom_dev);
-  float4 *scratch = base + texels;
-  const float4 *prev = reinterpret_cast<const float4 *>(in_device);
-  float4 *cur = base;
-  const dim3 blk(32, 8);
-  for (int k = 1; k <= levels; ++k) {
-    float4 *Dk = cur, *Bk = cur + (size_t)w[k] * h[k];
-    const dim3 g((w[k] + 31) / 32, (h[k] + 7) / 8);
-    bloom_down_kernel<<<g, blk, 0, s>>>(prev, w[k - 1], h[k - 1], Dk, w[k], h[k]);
-    bloom_blur_kernel<<<g, blk, 0, s>>>(Dk, scratch, w[k], h[k], 0);
-    bloom_blur_kernel<<<g, blk, 0, s>>>(scratch, Bk, w[k], h[k], 1);
-    L.lev[k] = Bk;
-    prev = Dk;
-    cur = Bk + (size_t)w[k] * h[k];
-  }
-  bloom_composite_kernel<<<dim3((width + 31) / 32, (height + 7) / 8), blk, 0, s>>>(
-      reinterpret_cast<const float4 *>(in_device), reinterpret_cast<float4 *>(out_device), width, height, L);
-  count_launch(ctx, 3 * levels + 1);
+  P.bar = ctx->bloom_bar;
+  P.status = ctx->status_dev;
+  P.wait_ns = 100000000ull;  // 0.1 s: a level takes microseconds
+  BH_CUDA(cudaMemsetAsync(ctx->bloom_bar, 0, sizeof(unsigned), s));
+  void *args[] = {&P};
+  BH_CUDA(cudaLaunchCooperativeKernel((const void *)bloom_kernel, dim3(coop_blocks[ctx->device]),
+                                      dim3(kBloomThreads), args, kBloomSmem, s));
+  count_launch(ctx, 1);
   BH_CUDA(cudaGetLastError());
   return BH_OK;
 }

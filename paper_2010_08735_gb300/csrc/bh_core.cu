@@ -46,10 +46,11 @@ bh_status check_status(bh_ctx *ctx, cudaStream_t s) {
   BH_CUDA(cudaMemcpyAsync(&st, ctx->status_dev, sizeof st, cudaMemcpyDeviceToHost, s));
   BH_CUDA(cudaStreamSynchronize(s));
   if (st) {
-    set_error("kernel status word 0x%x (%s%s)", st, (st & kStatusMbarTimeout) ? "table load timed out " : "",
+    set_error("kernel status word 0x%x (%s%s%s)", st, (st & kStatusMbarTimeout) ? "table load timed out " : "",
+              (st & kStatusBarrierTimeout) ? "grid barrier timed out " : "",
               (st & kStatusBadIndex) ? "index out of range" : "");
     BH_CUDA(cudaMemsetAsync(ctx->status_dev, 0, sizeof(unsigned), s));
-    return (st & kStatusMbarTimeout) ? BH_ERR_TIMEOUT : BH_ERR_DEVICE_STATUS;
+    return (st & (kStatusMbarTimeout | kStatusBarrierTimeout)) ? BH_ERR_TIMEOUT : BH_ERR_DEVICE_STATUS;
   }
   return BH_OK;
 }
@@ -524,6 +525,7 @@ extern "C" void bh_destroy(bh_ctx *c) {
   if (c->cam_dev) cudaFree(c->cam_dev);
   if (c->frame_dev) cudaFree(c->frame_dev);
   if (c->bloom_dev) cudaFree(c->bloom_dev);
+  if (c->bloom_bar) cudaFree(c->bloom_bar);
   if (c->orb_outs_host) cudaFreeHost(c->orb_outs_host);
   if (c->orb_outs_dev) cudaFree(c->orb_outs_dev);
   if (c->orb_cams_dev) cudaFree(c->orb_cams_dev);

@@ -40,6 +40,7 @@ constexpr int kMaxParticles = 256;  // animated disc: shared memory holds 32 byt
 // Status word bits written by kernels (never a trap or an assert).
 constexpr unsigned kStatusMbarTimeout = 1u;
 constexpr unsigned kStatusBadIndex = 2u;
+constexpr unsigned kStatusBarrierTimeout = 4u;  // a bounded grid-barrier wait gave up
 
 void set_error(const char *fmt, ...);
 bh_status cuda_fail(cudaError_t e, const char *what);
@@ -119,6 +120,7 @@ struct bh_ctx {
   size_t frame_cap = 0;
   void *bloom_dev = nullptr;          // bh_bloom: mip pyramid scratch
   size_t bloom_cap = 0;
+  unsigned *bloom_bar = nullptr;      // bh_bloom: grid-barrier counter
   bh::RenderTuning tuning;
   bh::ServeState *serve = nullptr;
   int inject_table_wait = 0;          // bh_inject_fault: next render's table wait never completes
