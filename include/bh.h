@@ -78,9 +78,14 @@ bh_status bh_check_status(bh_ctx *ctx, void *stream);
 /* Failure detection tests: make the next render launch of this context, after
  * its tables have landed, also wait on a barrier that nothing arrives at (kind
  * BH_FAULT_TABLE_WAIT), so that its bounded wait (2 ms) runs out, the blocks
- * skip their tiles and bh_check_status reports BH_ERR_TIMEOUT; the context
- * stays usable.  No fault, trap or hang is produced. */
+ * skip their tiles and bh_check_status reports BH_ERR_TIMEOUT; or make one
+ * block of the next bloom launch never arrive at its first grid barrier (kind
+ * BH_FAULT_BLOOM_BARRIER), so that every block's bounded barrier wait (2 ms)
+ * runs out and the blocks stop (the output is left unfinished) and
+ * bh_check_status reports BH_ERR_TIMEOUT.  The context stays usable.  No
+ * fault, trap or hang is produced. */
 #define BH_FAULT_TABLE_WAIT 1
+#define BH_FAULT_BLOOM_BARRIER 2
 bh_status bh_inject_fault(bh_ctx *ctx, int kind);
 
 /* Issue rates of the SMs of CUDA device `device`, measured by the library's

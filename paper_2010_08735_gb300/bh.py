@@ -225,6 +225,7 @@ def bh_destroy(ctx: int) -> None:
 
 
 BH_FAULT_TABLE_WAIT = 1
+BH_FAULT_BLOOM_BARRIER = 2
 
 
 def bh_check_status(ctx: int, stream=None) -> int:

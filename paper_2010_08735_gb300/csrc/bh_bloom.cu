@@ -54,6 +54,7 @@ struct BloomParams {
   unsigned *bar;        // grid-barrier arrival counter (zero at launch)
   unsigned *status;
   unsigned long long wait_ns;
+  int inject;           // fault injection: block 0 never arrives at the first barrier
 };
 
 // Grid-wide barrier for a cooperative launch (every block resident): each
@@ -65,7 +66,7 @@ __device__ bool grid_barrier(const BloomParams &P, unsigned phase) {
   __shared__ int ok;
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(P.bar, 1u);
+    if (!(P.inject && phase == 1 && blockIdx.x == 0)) atomicAdd(P.bar, 1u);
     const unsigned target = gridDim.x * phase;
     unsigned long long t0, t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
@@ -286,6 +287,11 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
   P.bar = ctx->bloom_bar;
   P.status = ctx->status_dev;
   P.wait_ns = 100000000ull;  // 0.1 s: a level takes microseconds
+  if (ctx->inject_bloom_barrier) {
+    P.inject = 1;
+    P.wait_ns = 2000000ull;  // 2 ms
+    ctx->inject_bloom_barrier = 0;
+  }
   BH_CUDA(cudaMemsetAsync(ctx->bloom_bar, 0, sizeof(unsigned), s));
   void *args[] = {&P};
   BH_CUDA(cudaLaunchCooperativeKernel((const void *)bloom_kernel, dim3(coop_blocks[ctx->device]),

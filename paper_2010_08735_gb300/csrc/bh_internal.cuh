@@ -124,6 +124,7 @@ struct bh_ctx {
   bh::RenderTuning tuning;
   bh::ServeState *serve = nullptr;
   int inject_table_wait = 0;          // bh_inject_fault: next render's table wait never completes
+  int inject_bloom_barrier = 0;       // bh_inject_fault: next bloom's first grid barrier is never complete
   std::mutex mu;
 };
 

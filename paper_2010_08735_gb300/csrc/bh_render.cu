@@ -653,8 +653,13 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         const float4 c000 = __ldg(cb), c100 = __ldg(cb + si), c010 = __ldg(cb + sj), c110 = __ldg(cb + sj + si);
         const float4 c001 = __ldg(cb + sk), c101 = __ldg(cb + sk + si), c011 = __ldg(cb + sk + sj),
                      c111 = __ldg(cb + sk + sj + si);
+        // packed f32x2 lerps: (x, y) and (z, pad) of each float4 texel at once
         auto lerp3 = [](float t, float4 a, float4 b) {
-          return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), fmaf(t, b.z - a.z, a.z), 0.f);
+          const float2 t2 = make_float2(t, t), m1 = make_float2(-1.f, -1.f);
+          const float2 axy = make_float2(a.x, a.y), azw = make_float2(a.z, a.w);
+          const float2 xy = __ffma2_rn(t2, __ffma2_rn(axy, m1, make_float2(b.x, b.y)), axy);
+          const float2 zw = __ffma2_rn(t2, __ffma2_rn(azw, m1, make_float2(b.z, b.w)), azw);
+          return make_float4(xy.x, xy.y, zw.x, zw.y);
         };
         const float4 cy0 = lerp3(ty2, lerp3(tx2, c000, c100), lerp3(tx2, c010, c110));
         const float4 cy1 = lerp3(ty2, lerp3(tx2, c001, c101), lerp3(tx2, c011, c111));
@@ -1490,8 +1495,9 @@ extern "C" bh_status bh_render_orbits(bh_ctx *ctx, const bh_tables *t, const bh_
 
 extern "C" bh_status bh_inject_fault(bh_ctx *ctx, int kind) {
   if (!ctx) { set_error("bh_inject_fault: NULL context"); return BH_ERR_INVALID_ARG; }
-  if (kind != BH_FAULT_TABLE_WAIT) { set_error("bh_inject_fault: unknown kind %d", kind); return BH_ERR_INVALID_ARG; }
-  ctx->inject_table_wait = 1;
+  if (kind == BH_FAULT_TABLE_WAIT) ctx->inject_table_wait = 1;
+  else if (kind == BH_FAULT_BLOOM_BARRIER) ctx->inject_bloom_barrier = 1;
+  else { set_error("bh_inject_fault: unknown kind %d", kind); return BH_ERR_INVALID_ARG; }
   return BH_OK;
 }
 

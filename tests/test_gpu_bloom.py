@@ -105,3 +105,25 @@ def test_bloom_rejects_bad_arguments(ctx):
         bh.bh_bloom(ctx, buf, buf, 0, 8, np.ones(2))
     with pytest.raises(bh.BhError):
         bh.bh_bloom_weights(0.0, 8, 2)
+
+
+def test_bloom_barrier_timeout_is_reported_and_context_recovers(ctx):
+    """Failure detection without a GPU fault: one block of the next bloom never
+    arrives at its first grid barrier (bh_inject_fault); every block's bounded
+    wait (2 ms) runs out, the blocks stop, bh_check_status reports
+    BH_ERR_TIMEOUT, and the next bloom on the context is correct."""
+    H, W = 120, 200
+    img = hdr_frame(H, W, 5)
+    w = bh.bh_bloom_weights(math.radians(60), H, 3)
+    inp = torch.from_numpy(img).cuda()
+    out = torch.zeros_like(inp)
+    bh.bh_inject_fault(ctx, bh.BH_FAULT_BLOOM_BARRIER)
+    bh.bh_bloom(ctx, inp, out, W, H, w)
+    torch.cuda.synchronize()
+    with pytest.raises(bh.BhError) as ei:
+        bh.bh_check_status(ctx)
+    assert ei.value.status == bh.BH_ERR_TIMEOUT
+    bh.bh_bloom(ctx, inp, out, W, H, w)
+    torch.cuda.synchronize()
+    assert bh.bh_check_status(ctx) == bh.BH_OK
+    assert compare(out.cpu().numpy(), ob.bloom(img, w)) <= BLOOM_REL
