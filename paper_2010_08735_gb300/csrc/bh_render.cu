@@ -300,39 +300,48 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float d2 = fmaf(C.R[6], ds0, fmaf(C.R[7], ds1, C.R[8] * ds2));
     const float x0 = C.x[0], x1 = C.x[1], x2 = C.x[2];
     float c0 = fmaf(x1, d2, -x2 * d1), c1 = fmaf(x2, d0, -x0 * d2), c2 = fmaf(x0, d1, -x1 * d0);
-    float cn = sqrtf(fmaf(c0, c0, fmaf(c1, c1, c2 * c2)));
+    const float cn2 = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
+    const float icn = rsqrtf(fmaxf(cn2, 1e-38f));  // 1/|e_x' ^ d| (guarded for radial beams)
     float cosd = fmaf(x0, d0, fmaf(x1, d1, x2 * d2));
-    float dd = sqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
-    float delta = atan2f(cn, cosd);
+    const float dd2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+    // delta itself is needed only for the debug channels: the disc hits use
+    // delta - alpha, one angle (below)
+    const float delta = DEBUG ? atan2f(cn2 * icn, cosd) : 0.f;
     float z0, z1, z2;
-    if (cn < 1e-7f * dd) {
+    if (cn2 < 1e-14f * dd2) {
       z0 = C.zdeg[0]; z1 = C.zdeg[1]; z2 = C.zdeg[2];
     } else {
-      float ic = 1.f / cn;
-      z0 = c0 * ic; z1 = c1 * ic; z2 = c2 * ic;
+      z0 = c0 * icn; z1 = c1 * icn; z2 = c2 * icn;
     }
     // e_y' = e_z' ^ e_x' (its z component is not needed below)
     float y0 = fmaf(z1, x2, -z2 * x1), y1 = fmaf(z2, x0, -z0 * x2);
     bool alpha_ok = false;
-    float alpha = 0.f;
+    float dma = 0.f;             // delta - alpha: the angle from t to the beam in the ray plane
     float tsx = 0.f, tsy = 0.f;  // t in the disc plane (x, y): hits lie at +-t
     {
-      float t0 = -z1, t1 = z0;
-      float tn = sqrtf(fmaf(t0, t0, t1 * t1));
-      if (tn > 1e-12f) {
-        // t = +-(e_z ^ e_z')/|.| with t . e_y' >= 0; alpha = angle from e_x' to t
-        float ty_ = fmaf(t0, y0, t1 * y1) / tn, tx_ = fmaf(t0, x0, t1 * x1) / tn;
-        float sg = ty_ < 0.f ? -1.f : 1.f;
-        alpha = atan2f(sg * ty_, sg * tx_);
-        tsx = sg * t0 / tn;
-        tsy = sg * t1 / tn;
+      // t = +-(e_z ^ e_z')/|.| with t . e_y' >= 0 (Eq. alpha: alpha is the angle
+      // from e_x' to t, delta the angle from e_x' to the beam d, both towards
+      // e_y'); delta - alpha = atan2((t ^ d) . e_z', t . d), t's length and d's
+      // length cancelling
+      const float t0 = -z1, t1 = z0;
+      const float tn2 = fmaf(t0, t0, t1 * t1);
+      if (tn2 > 1e-24f) {
+        const float sg = fmaf(t0, y0, t1 * y1) < 0.f ? -1.f : 1.f;
+        const float X = fmaf(t1 * d2, z0, fmaf(-t0 * d2, z1, fmaf(t0, d1, -t1 * d0) * z2));
+        const float Y = fmaf(t0, d0, t1 * d1);
+        dma = atan2f(sg * X, sg * Y);
+        if (MODE == kAnimated || DEBUG) {
+          const float itn = rsqrtf(tn2);
+          tsx = sg * t0 * itn;
+          tsy = sg * t1 * itn;
+        }
         alpha_ok = true;
       }
     }
 
     // ---- TRACERAY (Algorithm 1)
     const float u = C.u;
-    float udot = -u * cosd / fmaxf(cn, 1e-30f);
+    float udot = -u * cosd * icn;
     float um = u - 2.f / 3.f;
     float em = fmaf(udot, udot, -um * um * (u + 1.f / 3.f));  // e^2 - mu
     float e2 = kMuF + em;
@@ -405,7 +414,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           tcam = t_of_R(d_bilinear(P.DTt, dn, fx, yv * (dn - 1), xlo, xhi, chk), u);
           if (em < 0.f) tapsis = t_of_R(d_bilinear(P.DTt, dn, fx, (float)(dn - 1), xlo, xhi, chk), ua);
         }
-        float phi = fmaf((float)s, alpha, Dl + (s == 1 ? kPiF - delta : delta));
+        float phi = Dl + (s == 1 ? kPiF - dma : dma);
         float turns0 = floorf(phi / kPiF);
         float phi0 = fmaf(-kPiF, turns0, phi);
         const float u0 = phi0 < phia ? ulook(phi0) : 0.f;
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     // sum delta + turn is never rounded, which keeps d' to a few 1e-8.
     float st_, ct_;
     sincosf(turn, &st_, &ct_);
-    float idd = 1.f / dd;
+    float idd = rsqrtf(dd2);
     float b0 = d0 * idd, b1 = d1 * idd, b2 = d2 * idd;
     float n0 = fmaf(z1, b2, -z2 * b1), n1 = fmaf(z2, b0, -z0 * b2), n2 = fmaf(z0, b1, -z1 * b0);
     float dp0 = captured ? 0.f : fmaf(ct_, b0, st_ * n0);
@@ -513,9 +522,9 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     if (!anycap && P.cube) {
       float cq0 = fmaf(qw1, qh2, -qw2 * qh1), cq1 = fmaf(qw2, qh0, -qw0 * qh2), cq2 = fmaf(qw0, qh1, -qw1 * qh0);
       float cd0 = fmaf(dw1, dh2, -dw2 * dh1), cd1 = fmaf(dw2, dh0, -dw0 * dh2), cd2 = fmaf(dw0, dh1, -dw1 * dh0);
-      float den = sqrtf(fmaf(cd0, cd0, fmaf(cd1, cd1, cd2 * cd2)));
-      if (den > 0.f) {
-        omega = sqrtf(fmaf(cq0, cq0, fmaf(cq1, cq1, cq2 * cq2))) / den;
+      const float den2 = fmaf(cd0, cd0, fmaf(cd1, cd1, cd2 * cd2));
+      if (den2 > 0.f) {
+        omega = sqrtf(fmaf(cq0, cq0, fmaf(cq1, cq1, cq2 * cq2))) * rsqrtf(den2);
         float ax = fabsf(dp0), ay = fabsf(dp1), az = fabsf(dp2);
         float sc, tc, ma, dmaw, dmah, dscw, dsch, dtcw, dtch;
         if (ax >= ay && ax >= az) {
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float cS = S * sL, cT = T * sL, hsL = hs * sL, htL = ht * sL;
         float a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
         float det = fmaf(a11, a22, -a12 * a21);
-        if (fabsf(det) > 1e-6f * sqrtf(fmaf(a11, a11, a21 * a21) * fmaf(a12, a12, a22 * a22)) &&
+        if (det * det > 1e-12f * (fmaf(a11, a11, a21 * a21) * fmaf(a12, a12, a22 * a22)) &&
             check(L >= 0 && L < P.cube_levels && L < kMaxLevels && face >= 0 && face < 6)) {
           float id = 1.f / det;
           float i11 = a22 * id, i12 = -a12 * id, i21 = -a21 * id, i22 = a11 * id;
