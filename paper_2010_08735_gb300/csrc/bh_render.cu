@@ -24,11 +24,11 @@ constexpr int kMaxLevels = 14;
 // Per-camera constants, computed on the host in FP64 (Eq. staticbasis,
 // Eq. camerabasis, the boost B(v) of Appendix C, Eq. d) and rounded to float.
 struct CamConst {
-  float Ot[9];      // O^T: camera (e_w, e_h, e_d) components -> boosted (r', theta', phi') components
+  float M[9];       // R O^T: camera (e_w, e_h, e_d) components -> pseudo-Cartesian components, where
+                    // R (static orthonormal -> pseudo-Cartesian) has columns sqrt(1-u) r^, theta^, phi^
   float w[3];       // unit velocity direction on the camera axes (0 if v = 0)
-  float vhat[3];    // unit velocity direction on (e_r, e_theta, e_phi) (0 if v = 0)
+  float rv[3];      // R v^: the unit velocity direction in pseudo-Cartesian components (0 if v = 0)
   float beta, inv_gamma2;
-  float R[9];       // static orthonormal -> pseudo-Cartesian: columns sqrt(1-u) r^, theta^, phi^
   float x[3];       // e_x' = position direction r^
   float zdeg[3];    // e_z' for radial beams (reading C8)
   float gamma, f, u, inv_sqrt_1mu;
@@ -280,24 +280,27 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     // n.v^ - beta = (|q|^2/gamma^2 - |q x w|^2) / (|q| (q.w + beta |q|)) for
     // forward beams, free of the cancellation of n.v^ - beta near 1 - beta.
     float wq = fmaf(C.w[0], qw, fmaf(C.w[1], qh, C.w[2] * qd));
-    float dpar;
+    float dpar, pxw = 0.f;  // |q x w|^2 (forward beams)
     if (wq > 0.f) {
       float x0_ = fmaf(qh, C.w[2], -qd * C.w[1]), x1_ = fmaf(qd, C.w[0], -qw * C.w[2]),
             x2_ = fmaf(qw, C.w[1], -qh * C.w[0]);
       float c2 = fmaf(x0_, x0_, fmaf(x1_, x1_, x2_ * x2_));
+      pxw = c2;
       dpar = C.gamma * (fmaf(qq, C.inv_gamma2, -c2) / (nq * fmaf(C.beta, nq, wq)));
     } else {
       dpar = C.gamma * fmaf(wq, inv, -C.beta);
     }
+    // the backward direction on the static frame is ds = O^T p + dpar v^ with p
+    // (n's part across v) orthogonal to v^, so |ds|^2 = |p|^2 + dpar^2, |p|^2 =
+    // |q x w|^2 / |q|^2 (the forward branch has |q x w|^2 already)
     float p0 = fmaf(-wq, C.w[0], qw) * inv, p1 = fmaf(-wq, C.w[1], qh) * inv, p2 = fmaf(-wq, C.w[2], qd) * inv;
-    float ds0 = fmaf(C.Ot[0], p0, fmaf(C.Ot[1], p1, fmaf(C.Ot[2], p2, dpar * C.vhat[0])));
-    float ds1 = fmaf(C.Ot[3], p0, fmaf(C.Ot[4], p1, fmaf(C.Ot[5], p2, dpar * C.vhat[1])));
-    float ds2 = fmaf(C.Ot[6], p0, fmaf(C.Ot[7], p1, fmaf(C.Ot[8], p2, dpar * C.vhat[2])));
-    float dsn = sqrtf(fmaf(ds0, ds0, fmaf(ds1, ds1, ds2 * ds2)));
-    float dcam = C.gamma * fmaf(C.beta, dpar / dsn, 1.f);
-    float d0 = fmaf(C.R[0], ds0, fmaf(C.R[1], ds1, C.R[2] * ds2));
-    float d1 = fmaf(C.R[3], ds0, fmaf(C.R[4], ds1, C.R[5] * ds2));
-    float d2 = fmaf(C.R[6], ds0, fmaf(C.R[7], ds1, C.R[8] * ds2));
+    const float wqi = wq * inv;
+    const float pp = wq > 0.f ? pxw * (inv * inv) : fmaf(-wqi, wqi, 1.f);
+    float dcam = C.gamma * fmaf(C.beta, dpar * rsqrtf(fmaf(dpar, dpar, pp)), 1.f);
+    // pseudo-Cartesian beam direction d = R ds = (R O^T) p + dpar (R v^)
+    float d0 = fmaf(C.M[0], p0, fmaf(C.M[1], p1, fmaf(C.M[2], p2, dpar * C.rv[0])));
+    float d1 = fmaf(C.M[3], p0, fmaf(C.M[4], p1, fmaf(C.M[5], p2, dpar * C.rv[1])));
+    float d2 = fmaf(C.M[6], p0, fmaf(C.M[7], p1, fmaf(C.M[8], p2, dpar * C.rv[2])));
     const float x0 = C.x[0], x1 = C.x[1], x2 = C.x[2];
     float c0 = fmaf(x1, d2, -x2 * d1), c1 = fmaf(x2, d0, -x0 * d2), c2 = fmaf(x0, d1, -x1 * d0);
     const float cn2 = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
@@ -380,19 +383,24 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
       }
       if (alpha_ok && P.disc_on) {
-        float e = sqrtf(e2);
-        float ux = 1.f / fmaf(6.f, e2, 1.f);
-        float yk = fmaf(6.f * e2, e, 1.f) / (3.f * (1.f + e2));
+        // Appendix A coordinates of U: x = 1/(1 + 6e^2), y = phi (1 + 6e^3)/(3 (1 + e^2)),
+        // from one reciprocal; y's scale folds in the texel count
+        const float e = sqrtf(e2);
+        const float a6 = fmaf(6.f, e2, 1.f), a3 = 3.f * (1.f + e2);
+        const float iq = 1.f / (a6 * a3);
+        const float ux = a3 * iq;
+        const float yk = fmaf(6.f * e2, e, 1.f) * (a6 * iq) * (float)(P.u_nphi - 1);
         float fxu = fminf(fmaxf(ux * (P.u_ne - 1), 0.f), (float)(P.u_ne - 1));
         int ui0 = (int)fxu, ui1 = min(ui0 + 1, P.u_ne - 1);
         float utx = fxu - ui0;
         auto ulook = [&](float ph) {
-          float fy = fminf(fmaxf(ph * yk * (P.u_nphi - 1), 0.f), (float)(P.u_nphi - 1));
+          float fy = fminf(fmaxf(ph * yk, 0.f), (float)(P.u_nphi - 1));
           int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
           float ty2 = fy - j0;
           if (!check(j0 >= 0 && j1 < P.u_nphi && ui0 >= 0 && ui1 < P.u_ne)) return 0.f;
-          float a = sm_tab(s_U, j0 * P.u_ne + ui0), b = sm_tab(s_U, j0 * P.u_ne + ui1);
-          float c = sm_tab(s_U, j1 * P.u_ne + ui0), d = sm_tab(s_U, j1 * P.u_ne + ui1);
+          const int b0 = j0 * P.u_ne + ui0, du = ui1 - ui0, dv = (j1 - j0) * P.u_ne;
+          float a = sm_tab(s_U, b0), b = sm_tab(s_U, b0 + du);
+          float c = sm_tab(s_U, b0 + dv), d = sm_tab(s_U, b0 + dv + du);
           float lo = fmaf(utx, b - a, a), hi = fmaf(utx, d - c, c);
           return fmaf(ty2, hi - lo, lo);
         };
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float tcam = 0.f, tapsis = 0.f;
         auto t_of_R = [](float R, float uu) { return R - 1.f / uu + logf(uu / (1.f - uu)); };
         auto ulookT = [&](float ph) {
-          float fy = fminf(fmaxf(ph * yk * (P.u_nphi - 1), 0.f), (float)(P.u_nphi - 1));
+          float fy = fminf(fmaxf(ph * yk, 0.f), (float)(P.u_nphi - 1));
           int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
           float ty2 = fy - j0;
           if (!check(j0 >= 0 && j1 < P.u_nphi && ui0 >= 0 && ui1 < P.u_ne)) return 0.f;
@@ -541,11 +549,11 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           else { face = 5; sc = -dp0; tc = -dp1; dmaw = -dw2; dmah = -dh2; dscw = -dw0; dsch = -dh0; dtcw = -dw1; dtch = -dh1; }
         }
         const int N = P.cube_n;
-        float hN = 0.5f * N, ima = 1.f / ma;
+        float hN = 0.5f * N, ima = 1.f / ma, hNi = hN * ima;
         float sr = sc * ima, tr = tc * ima;
         float S = (sr + 1.f) * hN, T = (tr + 1.f) * hN;
-        float Jsw = hN * fmaf(-sr, dmaw, dscw) * ima, Jsh = hN * fmaf(-sr, dmah, dsch) * ima;
-        float Jtw = hN * fmaf(-tr, dmaw, dtcw) * ima, Jth = hN * fmaf(-tr, dmah, dtch) * ima;
+        float Jsw = hNi * fmaf(-sr, dmaw, dscw), Jsh = hNi * fmaf(-sr, dmah, dsch);
+        float Jtw = hNi * fmaf(-tr, dmaw, dtcw), Jth = hNi * fmaf(-tr, dmah, dtch);
         float hs = fabsf(Jsw) + fabsf(Jsh), ht = fabsf(Jtw) + fabsf(Jth);
         float hm = fmaxf(hs, ht);
         // smallest level L with 2 hm <= 8 * 2^L (at most 9x9 texels, C17): from
@@ -560,7 +568,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           L = min(L, P.cube_levels - 1);
         }
         level = L;
-        float sL = 1.f / (float)(1 << L);
+        const float sL = __int_as_float((127 - L) << 23);  // 2^-L
         int NL = N >> L;
         float cS = S * sL, cT = T * sL, hsL = hs * sL, htL = ht * sL;
         float a11 = Jsw * sL, a12 = Jsh * sL, a21 = Jtw * sL, a22 = Jth * sL;
@@ -571,8 +579,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           float i11 = a22 * id, i12 = -a12 * id, i21 = -a21 * id, i22 = a11 * id;
           int i0 = max((int)floorf(cS - hsL), 0), i1 = min((int)floorf(cS + hsL), NL - 1);
           int j0 = max((int)floorf(cT - htL), 0), j1 = min((int)floorf(cT + htL), NL - 1);
-          const uint2 *rec = P.cube + P.level_off[L] + (long long)face * NL * NL;
-          float lscale = (float)(1 << (2 * L));
+          const uint2 *rec = P.cube + P.level_off[L] + face * NL * NL;
+          const float lscale = __int_as_float((127 + 2 * L) << 23);  // 4^L
           // star at (ii + (ps + 1/2)/256, jj + (pt + 1/2)/256) in level-L texels
           const float q11 = i11 * (1.f / 256.f), q12 = i12 * (1.f / 256.f);
           const float q21 = i21 * (1.f / 256.f), q22 = i22 * (1.f / 256.f);
@@ -859,19 +867,20 @@ __host__ __device__ static void camera_constants(const bh_camera *c, CamConst *k
   if (vn > 0.0)
     for (int j = 0; j < 3; ++j) vh[j] = v[j] / vn;
   for (int j = 0; j < 3; ++j) {
-    for (int col = 0; col < 3; ++col) k->Ot[j * 3 + col] = (float)c->orient[col * 3 + j];
     double wc = 0.0;
     for (int m = 0; m < 3; ++m) wc += c->orient[j * 3 + m] * vh[m];
     k->w[j] = (float)wc;
-    k->vhat[j] = (float)vh[j];
   }
   k->beta = (float)vn;
   k->inv_gamma2 = (float)(1.0 - v2);
   double s1 = sqrt(1.0 - u);
   for (int r = 0; r < 3; ++r) {
-    k->R[r * 3 + 0] = (float)(s1 * rh[r]);
-    k->R[r * 3 + 1] = (float)th[r];
-    k->R[r * 3 + 2] = (float)ph[r];
+    // row r of R: (sqrt(1-u) r^, theta^, phi^) components r; M = R O^T, rv = R v^
+    const double Rr[3] = {s1 * rh[r], th[r], ph[r]};
+    for (int col = 0; col < 3; ++col)
+      k->M[r * 3 + col] = (float)(Rr[0] * c->orient[col * 3 + 0] + Rr[1] * c->orient[col * 3 + 1] +
+                                  Rr[2] * c->orient[col * 3 + 2]);
+    k->rv[r] = (float)(Rr[0] * vh[0] + Rr[1] * vh[1] + Rr[2] * vh[2]);
     k->x[r] = (float)rh[r];
   }
   // radial beams (reading C8): e_z' = x ^ (least-aligned axis) / |.|
