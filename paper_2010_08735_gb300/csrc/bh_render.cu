@@ -516,9 +516,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     float dp2 = captured ? 0.f : fmaf(ct_, b2, st_ * n2);
     unsigned capbits = __ballot_sync(0xffffffffu, captured);
     bool anycap = ((capbits >> (lane & ~3)) & 0xfu) != 0u;
-    const bool colodd = lane & 1, rowodd = (lane >> 1) & 1;
-    auto dw = [&](float v) { float o = __shfl_xor_sync(0xffffffffu, v, 1); return colodd ? v - o : o - v; };
-    auto dh = [&](float v) { float o = __shfl_xor_sync(0xffffffffu, v, 2); return rowodd ? o - v : v - o; };
+    // Fine derivatives up to sign: the quad neighbour's value subtracted from
+    // this pixel's.  The signs (+1 on odd columns, -1 on odd rows) are left
+    // out: every use below is even in them -- |cross products| for
+    // Omega/Omega', |J| column sums for the half-extents, and the tent weights
+    // f(w) f(h), whose (w, h) only change sign with J's columns -- and a sign
+    // flip is exact in floating point.
+    auto dw = [&](float v) { return v - __shfl_xor_sync(0xffffffffu, v, 1); };
+    auto dh = [&](float v) { return v - __shfl_xor_sync(0xffffffffu, v, 2); };
     float dw0 = dw(dp0), dw1 = dw(dp1), dw2 = dw(dp2);
     float dh0 = dh(dp0), dh1 = dh(dp1), dh2 = dh(dp2);
     float qw0 = dw(q0), qw1 = dw(q1), qw2 = dw(q2);
