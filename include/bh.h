@@ -302,6 +302,16 @@ bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *tables, const bh_cubem
                             const bh_camera *camera, const bh_disc *disc,
                             const bh_shading *shading, float *out_rgba_host, void *stream);
 
+/* As bh_render_to_host, with the image as packed linear RGB: width*height*3
+ * floats, row-major, top row first (the alpha channel, always 1, is not
+ * sent: a quarter less over the host link).  Pinned memory the device can
+ * address is written by the kernel directly; when it is 16-byte aligned and
+ * width % 4 == 0, every warp stores its four 96-byte pixel-row runs as
+ * 16-byte chunks.  Synchronises `stream` before returning. */
+bh_status bh_render_to_host_rgb(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                                const bh_camera *camera, const bh_disc *disc,
+                                const bh_shading *shading, float *out_rgb_host, void *stream);
+
 /* Render n cameras of any sizes in one persistent launch driven by a tile
  * queue: outs[k] is camera k's device image (as bh_render).  The per-camera
  * constants are staged through the context.  Enqueued on `stream`. */

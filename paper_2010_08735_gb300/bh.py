@@ -96,6 +96,7 @@ def lib():
             "bh_render": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
             "bh_render_debug": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp, _vp],
             "bh_render_to_host": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
+            "bh_render_to_host_rgb": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
             "bh_render_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
                                 P(_vp), _vp],
             "bh_autotune_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
@@ -427,6 +428,22 @@ def bh_render_to_host(ctx, tables, cube, camera, disc, shading, out_host: np.nda
         p = out_host.data_ptr()
     _check(lib().bh_render_to_host(ctx, tables, cube, C.byref(cam), C.byref(d),
                                    C.byref(shading), p, _stream(stream)))
+
+
+def bh_render_to_host_rgb(ctx, tables, cube, camera, disc, shading, out_host, stream=None) -> None:
+    """As bh_render_to_host, into packed linear RGB (height, width, 3) float32."""
+    cam = _as(camera, make_camera)
+    d = _as(disc, make_disc)
+    if isinstance(out_host, np.ndarray):
+        assert out_host.dtype == np.float32 and out_host.flags["C_CONTIGUOUS"]
+        assert out_host.size >= cam.width * cam.height * 3
+        p = out_host.ctypes.data
+    else:  # torch CPU tensor (pinned for the direct path)
+        assert out_host.dtype.itemsize == 4 and out_host.is_contiguous()
+        assert out_host.numel() >= cam.width * cam.height * 3
+        p = out_host.data_ptr()
+    _check(lib().bh_render_to_host_rgb(ctx, tables, cube, C.byref(cam), C.byref(d),
+                                       C.byref(shading), p, _stream(stream)))
 
 
 def _cams(cameras):

@@ -533,6 +533,26 @@ def test_render_to_host_equals_device(ctx, gpu_tables, static_scene):
     assert torch.equal(pinned, dev.cpu())
 
 
+@pytest.mark.parametrize("W,H", [(80, 40), (97, 61), (1920, 1080)])
+def test_render_to_host_rgb_equals_device(ctx, gpu_tables, static_scene, W, H):
+    """Packed linear RGB on the host equals the RGB of the device frame, bit for
+    bit: widths divisible by 4 take the staged 16-byte-chunk stores, others the
+    per-pixel ones; pinned buffers are written by the kernel, pageable ones
+    receive a copy."""
+    cube, _ = static_scene
+    cam = synth.camera(10.0, 80.0, width=W, height=H)
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    dev = torch.zeros((H, W, 4), device="cuda")
+    bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, dev)
+    ref = dev.cpu().numpy()[..., :3]
+    pinned = torch.full((H, W, 3), -1.0, dtype=torch.float32).pin_memory()
+    bh.bh_render_to_host_rgb(ctx, gpu_tables, cube, cam, synth.disc(), sh, pinned)
+    assert np.array_equal(pinned.numpy(), ref)
+    pageable = np.full((H, W, 3), -1.0, dtype=np.float32)
+    bh.bh_render_to_host_rgb(ctx, gpu_tables, cube, cam, synth.disc(), sh, pageable)
+    assert np.array_equal(pageable, ref)
+
+
 def test_serve_results_equal_alone(ctx, gpu_tables, static_scene):
     """Continuous batching: frames submitted while others are in flight come
     out equal to the same frame rendered alone."""
