@@ -40,7 +40,7 @@ __constant__ float cBloomTaps[4];
 constexpr int kBloomTile = 32;                      // output texels per tile side
 constexpr int kBloomHalo = 3;                       // blur radius
 constexpr int kBloomSpan = kBloomTile + 2 * kBloomHalo;
-constexpr int kBloomThreads = 256;
+constexpr int kBloomThreads = 1024;
 constexpr size_t kBloomSmem = sizeof(float4) * (kBloomSpan * kBloomSpan + kBloomSpan * kBloomTile);
 
 struct BloomParams {
@@ -263,7 +263,7 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
     BH_CUDA(cudaMemcpyToSymbol(cBloomTaps, tf, sizeof tf));
     int per_sm = 0;
     BH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bloom_kernel, kBloomThreads, kBloomSmem));
-    coop_blocks[ctx->device] = std::max(1, std::min(per_sm, 4)) * ctx->sm_count;
+    coop_blocks[ctx->device] = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
     taps_ready[ctx->device] = true;
   }
   BloomParams P;
