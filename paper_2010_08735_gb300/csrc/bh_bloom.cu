@@ -37,7 +37,7 @@ static double psf_energy(double a, double b) {
 // 7-tap Gaussian of unit standard deviation, normalised (taps at -3..3)
 __constant__ float cBloomTaps[4];
 
-constexpr int kBloomTile = 32;                      // output texels per tile side
+constexpr int kBloomTile = 64;                      // output texels per tile side
 constexpr int kBloomHalo = 3;                       // blur radius
 constexpr int kBloomSpan = kBloomTile + 2 * kBloomHalo;
 constexpr int kBloomThreads = 1024;
@@ -103,72 +103,135 @@ __device__ __forceinline__ float4 box_texel(const BloomParams &P, int k, int x, 
                      0.25f * ((a.z + b.z) + (c.z + d.z)), 1.f);
 }
 
-// One launch for the whole bloom: for each level, every block takes 32x32
-// tiles, builds the box level over the tile and a 3-texel halo in shared
-// memory (storing the tile's own texels for the next level), blurs along x
-// then y there and stores the blurred tile; a grid barrier separates the
-// levels; then every pixel of the frame is composited.
+// Levels built in one pass from regions of the frame: a region is 64 x 64
+// texels of level 1 (128 x 128 pixels), 32 x 32 of level 2, ..., one texel of
+// level 7; a level-k texel's four children lie in its own region (clamped
+// children at an odd edge are the texel's own first child), so a block
+// reduces a region level by level in shared memory with no grid barrier.
+constexpr int kBloomRegionLevels = 7;
+
+// Blur (7 taps along x, then along y, clamped) of one 64x64 tile of level k,
+// its box texels read from global memory with a 3-texel halo.
+__device__ void blur_tile(const BloomParams &P, int k, int x0, int y0, float4 *sD, float4 *sH) {
+  const int w = P.w[k], h = P.h[k];
+  const float4 *Dk = P.D[k];
+  for (int i = threadIdx.x; i < kBloomSpan * kBloomSpan; i += blockDim.x) {
+    const int r = i / kBloomSpan, c = i - r * kBloomSpan;
+    const int x = min(max(x0 + c - kBloomHalo, 0), w - 1), y = min(max(y0 + r - kBloomHalo, 0), h - 1);
+    sD[i] = Dk[(size_t)y * w + x];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBloomSpan * kBloomTile; i += blockDim.x) {
+    const int r = i / kBloomTile, c = i - r * kBloomTile;
+    // taps past the level's edge read the clamped texel (the halo holds it
+    // only where the level continues)
+    const int x = x0 + c;
+    float rr = 0.f, gg = 0.f, bb = 0.f;
+#pragma unroll
+    for (int t = -3; t <= 3; ++t) {
+      const int xx = min(max(x + t, 0), w - 1) - x0 + kBloomHalo;
+      const float4 v = sD[r * kBloomSpan + xx];
+      const float kt = cBloomTaps[t < 0 ? -t : t];
+      rr = fmaf(kt, v.x, rr);
+      gg = fmaf(kt, v.y, gg);
+      bb = fmaf(kt, v.z, bb);
+    }
+    sH[i] = make_float4(rr, gg, bb, 1.f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBloomTile * kBloomTile; i += blockDim.x) {
+    const int r = i / kBloomTile, c = i - r * kBloomTile;
+    const int x = x0 + c, y = y0 + r;
+    if (x >= w || y >= h) continue;
+    float rr = 0.f, gg = 0.f, bb = 0.f;
+#pragma unroll
+    for (int t = -3; t <= 3; ++t) {
+      const int yy = min(max(y + t, 0), h - 1) - y0 + kBloomHalo;
+      const float4 v = sH[yy * kBloomTile + c];
+      const float kt = cBloomTaps[t < 0 ? -t : t];
+      rr = fmaf(kt, v.x, rr);
+      gg = fmaf(kt, v.y, gg);
+      bb = fmaf(kt, v.z, bb);
+    }
+    P.B[k][(size_t)y * w + x] = make_float4(rr, gg, bb, 1.f);
+  }
+  __syncthreads();
+}
+
+// One launch for the whole bloom, in three phases separated by grid
+// barriers: the box levels (regions of the frame reduced in shared memory;
+// levels past the seventh one grid-wide pass each), the blur of every tile of
+// every level, then the composite of every pixel.
 __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams P) {
   extern __shared__ float4 sb[];
   float4 *sD = sb;                              // kBloomSpan x kBloomSpan box texels
   float4 *sH = sb + kBloomSpan * kBloomSpan;    // kBloomSpan rows x kBloomTile: blurred along x
-  for (int k = 1; k <= P.n; ++k) {
-    const int w = P.w[k], h = P.h[k];
-    const int tx = (w + kBloomTile - 1) / kBloomTile, tiles = tx * ((h + kBloomTile - 1) / kBloomTile);
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-      const int x0 = (tile % tx) * kBloomTile, y0 = (tile / tx) * kBloomTile;
-      for (int i = threadIdx.x; i < kBloomSpan * kBloomSpan; i += blockDim.x) {
-        const int r = i / kBloomSpan, c = i - r * kBloomSpan;
-        const int x = x0 + c - kBloomHalo, y = y0 + r - kBloomHalo;
-        const float4 v = box_texel(P, k, x, y);
-        sD[i] = v;
-        if (r >= kBloomHalo && r < kBloomHalo + kBloomTile && c >= kBloomHalo && c < kBloomHalo + kBloomTile &&
-            x < w && y < h)
+  unsigned phase = 0;
+  if (P.n > 0) {
+    // ---- box levels 1..6 by regions (ping-pong halves of the shared buffer)
+    const int nr = min(P.n, kBloomRegionLevels);
+    const int rx = (P.w[1] + kBloomTile - 1) / kBloomTile, regions = rx * ((P.h[1] + kBloomTile - 1) / kBloomTile);
+    // level 1 fills the first kBloomTile^2 texels, level 2 the next quarter of that, and so on alternately
+    float4 *cur = sb + kBloomTile * kBloomTile, *nxt = sb;
+    for (int reg = blockIdx.x; reg < regions; reg += gridDim.x) {
+      const int gx = reg % rx, gy = reg / rx;
+      for (int k = 1; k <= nr; ++k) {
+        const int side = kBloomTile >> (k - 1);  // texels of level k per region side
+        const int w = P.w[k], h = P.h[k];
+        for (int i = threadIdx.x; i < side * side; i += blockDim.x) {
+          const int lx = i % side, ly = i / side;
+          const int x = gx * side + lx, y = gy * side + ly;
+          if (x >= w || y >= h) continue;
+          float4 v;
+          if (k == 1) {
+            v = box_texel(P, 1, x, y);
+          } else {
+            // children in the previous level's region buffer (side 2 * side)
+            const int pw = P.w[k - 1], ph = P.h[k - 1], ps = 2 * side;
+            const int cx0 = min(2 * x, pw - 1) - 2 * gx * side, cx1 = min(2 * x + 1, pw - 1) - 2 * gx * side;
+            const int cy0 = min(2 * y, ph - 1) - 2 * gy * side, cy1 = min(2 * y + 1, ph - 1) - 2 * gy * side;
+            const float4 a = cur[cy0 * ps + cx0], b = cur[cy0 * ps + cx1];
+            const float4 c = cur[cy1 * ps + cx0], d = cur[cy1 * ps + cx1];
+            v = make_float4(0.25f * ((a.x + b.x) + (c.x + d.x)), 0.25f * ((a.y + b.y) + (c.y + d.y)),
+                            0.25f * ((a.z + b.z) + (c.z + d.z)), 1.f);
+          }
+          nxt[i] = v;
           P.D[k][(size_t)y * w + x] = v;
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < kBloomSpan * kBloomTile; i += blockDim.x) {
-        const int r = i / kBloomTile, c = i - r * kBloomTile;
-        // taps past the level's edge read the clamped texel (the halo holds it
-        // only where the level continues)
-        const int x = x0 + c;
-        float rr = 0.f, gg = 0.f, bb = 0.f;
-#pragma unroll
-        for (int t = -3; t <= 3; ++t) {
-          const int xx = min(max(x + t, 0), w - 1) - x0 + kBloomHalo;
-          const float4 v = sD[r * kBloomSpan + xx];
-          const float kt = cBloomTaps[t < 0 ? -t : t];
-          rr = fmaf(kt, v.x, rr);
-          gg = fmaf(kt, v.y, gg);
-          bb = fmaf(kt, v.z, bb);
         }
-        sH[i] = make_float4(rr, gg, bb, 1.f);
+        __syncthreads();
+        float4 *t = cur;
+        cur = nxt;
+        nxt = t;
       }
-      __syncthreads();
-      for (int i = threadIdx.x; i < kBloomTile * kBloomTile; i += blockDim.x) {
-        const int r = i / kBloomTile, c = i - r * kBloomTile;
-        const int x = x0 + c, y = y0 + r;
-        if (x >= w || y >= h) continue;
-        float rr = 0.f, gg = 0.f, bb = 0.f;
-#pragma unroll
-        for (int t = -3; t <= 3; ++t) {
-          const int yy = min(max(y + t, 0), h - 1) - y0 + kBloomHalo;
-          const float4 v = sH[yy * kBloomTile + c];
-          const float kt = cBloomTaps[t < 0 ? -t : t];
-          rr = fmaf(kt, v.x, rr);
-          gg = fmaf(kt, v.y, gg);
-          bb = fmaf(kt, v.z, bb);
-        }
-        P.B[k][(size_t)y * w + x] = make_float4(rr, gg, bb, 1.f);
-      }
-      __syncthreads();
     }
-    if (!grid_barrier(P, (unsigned)k)) return;
+    // ---- levels past the region's depth: one grid-wide pass each
+    for (int k = kBloomRegionLevels + 1; k <= P.n; ++k) {
+      if (!grid_barrier(P, ++phase)) return;
+      const long long nt = (long long)P.w[k] * P.h[k];
+      for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / P.w[k]), x = (int)(i - (long long)y * P.w[k]);
+        P.D[k][i] = box_texel(P, k, x, y);
+      }
+    }
+    if (!grid_barrier(P, ++phase)) return;
+    // ---- blur every 64x64 tile of every level
+    int tiles_before[kBloomMaxLevels + 2];
+    tiles_before[1] = 0;
+    for (int k = 1; k <= P.n; ++k)
+      tiles_before[k + 1] = tiles_before[k] + ((P.w[k] + kBloomTile - 1) / kBloomTile) * ((P.h[k] + kBloomTile - 1) / kBloomTile);
+    for (int tile = blockIdx.x; tile < tiles_before[P.n + 1]; tile += gridDim.x) {
+      int k = 1;
+      while (tile >= tiles_before[k + 1]) ++k;
+      const int t = tile - tiles_before[k], tx = (P.w[k] + kBloomTile - 1) / kBloomTile;
+      blur_tile(P, k, (t % tx) * kBloomTile, (t / tx) * kBloomTile, sD, sH);
+    }
+    if (!grid_barrier(P, ++phase)) return;
   }
-  // composite at full resolution
+  // composite at full resolution, two pixels per thread and iteration (their
+  // loads in flight together)
   const int W = P.w[0], H = P.h[0];
-  const long long npx = (long long)W * H;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (long long)gridDim.x * blockDim.x) {
+  const long long npx = (long long)W * H, stride = (long long)gridDim.x * blockDim.x;
+  auto composite = [&](long long p, float4 &res) {
     const int y = (int)(p / W), x = (int)(p - (long long)y * W);
     const float4 c = P.in[p];
     float r = P.wt[0] * c.x, g = P.wt[0] * c.y, b = P.wt[0] * c.z;
@@ -191,7 +254,15 @@ __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams 
       g = fmaf(wk, lg, g);
       b = fmaf(wk, lb, b);
     }
-    P.out[p] = make_float4(r, g, b, 1.f);
+    res = make_float4(r, g, b, 1.f);
+  };
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += 2 * stride) {
+    float4 r0, r1;
+    const bool two = p + stride < npx;
+    composite(p, r0);
+    if (two) composite(p + stride, r1);
+    P.out[p] = r0;
+    if (two) P.out[p + stride] = r1;
   }
 }
 
@@ -261,6 +332,9 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
     float tf[4];
     for (int i = 0; i < 4; ++i) tf[i] = (float)(t[i] / sum);
     BH_CUDA(cudaMemcpyToSymbol(cBloomTaps, tf, sizeof tf));
+    static_assert(kBloomSmem >= sizeof(float4) * (kBloomTile * kBloomTile + kBloomTile * kBloomTile / 4),
+                  "the region ping-pong buffers fit in the blur tile's shared memory");
+    BH_CUDA(cudaFuncSetAttribute(bloom_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBloomSmem));
     int per_sm = 0;
     BH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bloom_kernel, kBloomThreads, kBloomSmem));
     coop_blocks[ctx->device] = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
