@@ -297,11 +297,27 @@ def oracle_leg(wk, gpu_frames, seconds=12.0):
                                scene32.cube_dtype)
     ref, dbg, _ = oracle.render(cam, disc, exact, exposure_stars=0.01, debug=True)
     mask = edge_mask(~np.isfinite(dbg[..., 2]), dbg[..., 3])
+    # the parity tests' full exclusion (reading C19): also mip-level and face
+    # decisions within 2 % / 2e-3 of their thresholds, degenerate footprints and
+    # star pixels whose RGB changes by more than 1 % for the 1e-6 rad an FP32
+    # escape direction can be off (oracle channels 6, 16, 17, 18, 8, 20-22)
+    lvl, hm = dbg[..., 6], dbg[..., 16]
+    has = lvl >= 0
+    ratio = np.where(has, 2 * hm / (8 * 2.0 ** np.maximum(lvl, 0)), 0.0)
+    prev = np.where(has & (lvl > 0), 2 * hm / (8 * 2.0 ** np.maximum(lvl - 1, 0)), 0.0)
+    floor = 1e-4 * max(np.abs(ref[..., :3]).max(), 1e-30)
+    sens = (dbg[..., 20:23] / np.maximum(np.abs(ref[..., :3]), floor)).max(-1)
+    shift_px = 1e-6 * np.sqrt(np.maximum(dbg[..., 8], 0.0)) / (cam["fov_y"] / cam["height"])
+    c19 = (mask | (has & (ratio > 0.98) & (ratio <= 1)) | (has & (lvl > 0) & (prev < 1.02)) |
+           (has & (dbg[..., 17] < 2e-3)) | (has & (dbg[..., 18] < 1e-5)) | (sens * shift_px > 1e-2))
     del dbg
     errors = {"workload": WORKLOAD, "reference": "FP64 oracle on the FP64 tables",
-              "mask": "pixels within 1 px of the shadow silhouette or a disc edge"}
+              "mask": "pixels within 1 px of the shadow silhouette or a disc edge",
+              "mask_c19": "that mask plus the parity tests' threshold-margin, degenerate and "
+                          "FP32-ill-conditioned star pixels (reading C19)"}
     for k, img in gpu_frames.items():
         errors[k] = rel_error(img, ref, mask)
+        errors[k + "_c19"] = rel_error(img, ref, c19)
     # table method vs the table-free 3D photon orbit (Sec. 4)
     W, H = cam["width"], cam["height"]
     th, ph = cam["theta"], cam["phi"]
