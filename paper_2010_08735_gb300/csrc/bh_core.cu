@@ -187,8 +187,7 @@ __device__ __forceinline__ __half to_storage<__half>(double v) { return __double
 
 // D(e,u) per texel: texel (i,j) holds the Appendix A coordinates
 // x = i/(n-1), y = j/(n-1) (reading C3).
-template <typename T>
-__global__ void precompute_D_kernel(int n, double *D64, T *Ds, double *DT64, float *DTs) {
+__global__ void precompute_D_kernel(int n, double *D64, double *DT64, float *DTs) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
   if (i >= n || j >= n) return;
@@ -224,7 +223,6 @@ __global__ void precompute_D_kernel(int n, double *D64, T *Ds, double *DT64, flo
     R = plunge_integral<true>(se, sqrt(e2), ta, tb);
   }
   D64[(size_t)j * n + i] = Delta;
-  Ds[(size_t)j * n + i] = to_storage<T>(Delta);
   DT64[(size_t)j * n + i] = R;
   DTs[(size_t)j * n + i] = (float)R;
 }
@@ -367,6 +365,17 @@ __global__ void precompute_U_kernel(int ne, int nphi, double *U64, T *Us, double
     UT64[(size_t)j * ne + i] = R;
     UTs[(size_t)j * ne + i] = (float)R;
   }
+}
+
+// The render copy of D, row-paired: texel (j, i) holds D(j, i) and
+// D(min(j+1, n-1), i) side by side, so a bilinear lookup is two loads.
+template <typename T>
+__global__ void pair_d_kernel(int n, const double *D64, T *Dp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n || j >= n) return;
+  const size_t o = (size_t)j * n + i;
+  Dp[2 * o] = to_storage<T>(D64[o]);
+  Dp[2 * o + 1] = to_storage<T>(D64[(size_t)min(j + 1, n - 1) * n + i]);
 }
 
 template <typename T>
@@ -562,7 +571,7 @@ static bh_status tables_alloc(bh_ctx *ctx, const bh_table_desc *desc, cudaStream
   size_t es = desc->storage == BH_F32 ? 4 : 2;
   cudaError_t e = cudaMalloc((void **)&t->D64, nd * 8);
   if (e == cudaSuccess) e = cudaMalloc((void **)&t->U64, nu * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&t->D, nd * es);
+  if (e == cudaSuccess) e = cudaMalloc(&t->D, 2 * nd * es);  // row-paired render copy
   if (e == cudaSuccess) e = cudaMalloc(&t->U, ((nu * es + 15) / 16) * 16);
   if (e == cudaSuccess) e = cudaMalloc((void **)&t->DT64, nd * 8);
   if (e == cudaSuccess) e = cudaMalloc((void **)&t->UT64, nu * 8);
@@ -593,16 +602,17 @@ extern "C" bh_status bh_precompute_tables(bh_ctx *ctx, const bh_table_desc *desc
   int n = desc->d_n;
   dim3 gd((n + 127) / 128, n);
   unsigned gu = (unsigned)((desc->u_ne * desc->u_nphi + 3) / 4);  // 4 warps (texels) per block
+  precompute_D_kernel<<<gd, 128, 0, s>>>(n, t->D64, t->DT64, t->DT);
   if (desc->storage == BH_F32) {
-    precompute_D_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D, t->DT64, t->DT);
+    pair_d_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D);
     precompute_U_kernel<float><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (float *)t->U, t->UT64,
                                                  t->UT);
   } else {
-    precompute_D_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D, t->DT64, t->DT);
+    pair_d_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D);
     precompute_U_kernel<__half><<<gu, 128, 0, s>>>(desc->u_ne, desc->u_nphi, t->U64, (__half *)t->U, t->UT64,
                                                   t->UT);
   }
-  count_launch(ctx, 2);
+  count_launch(ctx, 3);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { bh_tables_free(t); return cuda_fail(e, "precompute launch"); }
   st = colour_tables_launch(ctx, t, s);
@@ -620,11 +630,13 @@ bh_status tables_alloc_public(bh_ctx *ctx, const bh_table_desc *desc, bh_tables 
 // time channels from the FP64 values already on the device.
 bh_status tables_convert_storage(bh_ctx *ctx, bh_tables *t, cudaStream_t s) {
   size_t nd = (size_t)t->desc.d_n * t->desc.d_n, nu = (size_t)t->desc.u_ne * t->desc.u_nphi;
+  const int n = t->desc.d_n;
+  const dim3 gd((n + 127) / 128, n);
   if (t->desc.storage == BH_F32) {
-    convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (float *)t->D, nd);
+    pair_d_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D);
     convert_kernel<float><<<(nu + 255) / 256, 256, 0, s>>>(t->U64, (float *)t->U, nu);
   } else {
-    convert_kernel<__half><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (__half *)t->D, nd);
+    pair_d_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D);
     convert_kernel<__half><<<(nu + 255) / 256, 256, 0, s>>>(t->U64, (__half *)t->U, nu);
   }
   convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->DT64, t->DT, nd);
@@ -655,11 +667,13 @@ extern "C" bh_status bh_tables_upload(bh_ctx *ctx, const bh_table_desc *desc, co
   if (e == cudaSuccess) e = cudaMemsetAsync(t->DT, 0xff, nd * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->UT, 0xff, nu * 4, s);
   if (e == cudaSuccess) {
+    const int n = desc->d_n;
+    const dim3 gd((n + 127) / 128, n);
     if (desc->storage == BH_F32) {
-      convert_kernel<float><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (float *)t->D, nd);
+      pair_d_kernel<float><<<gd, 128, 0, s>>>(n, t->D64, (float *)t->D);
       convert_kernel<float><<<(nu + 255) / 256, 256, 0, s>>>(t->U64, (float *)t->U, nu);
     } else {
-      convert_kernel<__half><<<(nd + 255) / 256, 256, 0, s>>>(t->D64, (__half *)t->D, nd);
+      pair_d_kernel<__half><<<gd, 128, 0, s>>>(n, t->D64, (__half *)t->D);
       convert_kernel<__half><<<(nu + 255) / 256, 256, 0, s>>>(t->U64, (__half *)t->U, nu);
     }
     count_launch(ctx, 2);

@@ -85,6 +85,34 @@ constexpr float kMuF = 4.0f / 27.0f;
 constexpr int kDbgFloats = 20;  // debug values per pixel (five float4)
 constexpr float kPiF = 3.14159265358979f;
 
+// Texel pair (row j, row min(j+1, n-1)) of the row-paired D table.
+__device__ __forceinline__ float2 ld_pair(const float *p, int i) {
+  return __ldg(reinterpret_cast<const float2 *>(p) + i);
+}
+__device__ __forceinline__ float2 ld_pair(const __half *p, int i) {
+  return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p) + i));
+}
+
+// Bilinear lookup in the row-paired D table (texel (j, i) holds D at rows j
+// and min(j+1, n-1)): two loads, the x lerps of both rows as one packed f32x2
+// step.  Appendix A coordinates; x clamped to its branch (C2).
+template <typename DT>
+__device__ __forceinline__ float d_bilinear_pair(const DT *D, int n, float fx, float fy, int xlo, int xhi,
+                                                 unsigned *chk = nullptr) {
+  fx = fminf(fmaxf(fx, (float)xlo), (float)xhi);
+  fy = fminf(fmaxf(fy, 0.f), (float)(n - 1));
+  const int i0 = (int)fx, j0 = (int)fy;
+  const int i1 = min(i0 + 1, xhi);
+  if (chk && !(i0 >= 0 && j0 >= 0 && i1 < n && j0 < n && i0 <= i1)) {
+    atomicOr(chk, kStatusBadIndex);  // checked (debug) render: record and skip the access
+    return 0.f;
+  }
+  const float tx = fx - i0, ty = fy - j0;
+  const float2 p = ld_pair(D, j0 * n + i0), q = ld_pair(D, j0 * n + i1);  // (a, c), (b, d)
+  const float2 lh = __ffma2_rn(make_float2(tx, tx), __ffma2_rn(p, make_float2(-1.f, -1.f), q), p);
+  return fmaf(ty, lh.y - lh.x, lh.x);
+}
+
 // Bilinear D lookup at Appendix A coordinates; x clamped to its branch (C2).
 template <typename DT>
 __device__ __forceinline__ float d_bilinear(const DT *D, int n, float fx, float fy, int xlo, int xhi,
@@ -377,14 +405,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float g = fmaf(-u, u, fmaf(-ua, u, fmaf(-ua, ua, ua + u)));
         float om = g > 0.f ? udot * udot / (ua * g) : 1.f - u / ua;
         yv = 1.f - sqrtf(fmaxf(om, 0.f));
-        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
-        Da = d_bilinear(D, dn, fx, (float)(dn - 1), xlo, xhi, chk);
+        Dl = d_bilinear_pair(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
+        Da = d_bilinear_pair(D, dn, fx, (float)(dn - 1), xlo, xhi, chk);
         phia = Da + 0.5f * kPiF;
       } else {
         const float r23 = 0.81649658f, r13 = 0.57735027f;
         float sq = sqrtf(fabsf(um));
         yv = (r23 + (um >= 0.f ? sq : -sq)) / (r23 + r13);
-        Dl = d_bilinear(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
+        Dl = d_bilinear_pair(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
       }
       if (alpha_ok && P.disc_on) {
         // Appendix A coordinates of U: x = 1/(1 + 6e^2), y = phi (1 + 6e^3)/(3 (1 + e^2)),
@@ -605,9 +633,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           auto row_bits = [&](const int jj) {
             if (!check(jj >= 0 && jj < NL && w0i >= 0 && w0i + (straddle ? 1 : 0) < wpr)) return 0u;
             const unsigned *mrow = mrows + (jj * wpr + w0i);
-            unsigned long long win = __ldg(mrow);
-            if (straddle) win |= (unsigned long long)__ldg(mrow + 1) << 32;
-            return (unsigned)(win >> b0) & rowbits;
+            const unsigned lo = __ldg(mrow), hi = straddle ? __ldg(mrow + 1) : 0u;
+            return __funnelshift_r(lo, hi, b0) & rowbits;  // bits b0.. of the 64-bit window
           };
           const bool bf16 = P.cube_bf16;
           unsigned bits = j0 <= j1 ? row_bits(j0) : 0u;
