@@ -554,7 +554,25 @@ def run_ours(args):
             fn(ctx, tables, cube, orbit_camera(wk, s), disc, sh, host, stream)
         e2e[name] = ws * e2e_steps / (time.perf_counter() - t)
         del host
-    e2e_fps = e2e["rgb"]
+    # two frames in flight (bh_render_to_host_async): frame s renders while
+    # frame s - 1 is copied to the host; every frame is in host memory
+    # (bh_host_wait) inside the timed region
+    hosts = [torch.empty((H, W, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    for s in range(3):
+        bh.bh_host_wait(ctx, bh.bh_render_to_host_async(ctx, tables, cube, orbit_camera(wk, s), disc, sh,
+                                                        hosts[s & 1], True, stream))
+    t = time.perf_counter()
+    prev = None
+    for s in range(e2e_steps):
+        tk = bh.bh_render_to_host_async(ctx, tables, cube, orbit_camera(wk, s), disc, sh, hosts[s & 1], True,
+                                        stream)
+        if prev is not None:
+            bh.bh_host_wait(ctx, prev)
+        prev = tk
+    bh.bh_host_wait(ctx, prev)
+    e2e["rgb_async"] = ws * e2e_steps / (time.perf_counter() - t)
+    del hosts
+    e2e_fps = e2e["rgb_async"]
 
     # --- plain and served forms on equal terms: host wall clock per frame,
     # 2000 frames each, the same cameras, no L2 flush on either side
@@ -631,8 +649,9 @@ def run_ours(args):
         "issue_rates": rates,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": 200,
                 "d2h_bytes_per_step": W * H * 12, "frames": e2e_steps,
-                "api": "bh_render_to_host_rgb (packed linear RGB into pinned host memory)",
-                "rgba_frames_per_s": e2e["rgba"]},
+                "api": "bh_render_to_host_async + bh_host_wait (packed linear RGB into pinned host memory, "
+                       "two frames in flight: one renders while the other is copied)",
+                "one_at_a_time_frames_per_s": e2e["rgb"], "rgba_one_at_a_time_frames_per_s": e2e["rgba"]},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed_region": wall,

@@ -312,6 +312,29 @@ bh_status bh_render_to_host_rgb(bh_ctx *ctx, const bh_tables *tables, const bh_c
                                 const bh_camera *camera, const bh_disc *disc,
                                 const bh_shading *shading, float *out_rgb_host, void *stream);
 
+/* Frames to the host with two in flight: renders the frame into one of two
+ * context-owned device frames on `stream` and returns at once; the copy
+ * engine then moves it into out_host on a context-owned copy stream while
+ * the next call's frame renders into the other device frame (a device frame
+ * is rendered into again only after its previous copy has finished).
+ *  - out_host: pinned host memory (cudaHostAlloc, cudaHostRegister) of
+ *    width*height*4 floats (rgb = 0: RGBA as bh_render) or width*height*3
+ *    (rgb = 1: packed linear RGB as bh_render_to_host_rgb); it must stay
+ *    allocated and unread until bh_host_wait(ticket) returns.
+ *  - *ticket receives the frame's number (0, 1, 2, ... per context).
+ * Errors: BH_ERR_INVALID_ARG for NULL arguments, an invalid camera, rgb not
+ * 0 or 1, or pageable out_host (nothing is enqueued then).  The image is the
+ * one bh_render / bh_render_to_host_rgb produce for the same arguments. */
+bh_status bh_render_to_host_async(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
+                                  const bh_camera *camera, const bh_disc *disc,
+                                  const bh_shading *shading, float *out_host, int rgb, void *stream,
+                                  unsigned long long *ticket);
+
+/* Block until frame `ticket` of bh_render_to_host_async is in host memory
+ * (it may return after a later frame's copy, which implies this one's).
+ * BH_ERR_INVALID_ARG for a ticket that was never issued. */
+bh_status bh_host_wait(bh_ctx *ctx, unsigned long long ticket);
+
 /* Render n cameras of any sizes in one persistent launch driven by a tile
  * queue: outs[k] is camera k's device image (as bh_render).  The per-camera
  * constants are staged through the context.  Enqueued on `stream`. */

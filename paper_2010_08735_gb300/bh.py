@@ -97,6 +97,9 @@ def lib():
             "bh_render_debug": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp, _vp],
             "bh_render_to_host": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
             "bh_render_to_host_rgb": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, _vp],
+            "bh_render_to_host_async": [_vp, _vp, _vp, P(Camera), P(Disc), P(Shading), _vp, C.c_int, _vp,
+                                        P(C.c_ulonglong)],
+            "bh_host_wait": [_vp, C.c_ulonglong],
             "bh_render_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
                                 P(_vp), _vp],
             "bh_autotune_batch": [_vp, _vp, _vp, C.c_int, P(Camera), P(Disc), P(Shading),
@@ -444,6 +447,26 @@ def bh_render_to_host_rgb(ctx, tables, cube, camera, disc, shading, out_host, st
         p = out_host.data_ptr()
     _check(lib().bh_render_to_host_rgb(ctx, tables, cube, C.byref(cam), C.byref(d),
                                        C.byref(shading), p, _stream(stream)))
+
+
+def bh_render_to_host_async(ctx, tables, cube, camera, disc, shading, out_host, rgb=True, stream=None) -> int:
+    """Enqueue a frame to pinned host memory (packed RGB (height, width, 3) or
+    RGBA (height, width, 4) float32) with two frames in flight; returns the
+    frame's ticket for bh_host_wait.  out_host must stay untouched until then."""
+    cam = _as(camera, make_camera)
+    d = _as(disc, make_disc)
+    ch = 3 if rgb else 4
+    assert out_host.dtype.itemsize == 4 and out_host.is_contiguous()
+    assert out_host.numel() >= cam.width * cam.height * ch
+    t = C.c_ulonglong(0)
+    _check(lib().bh_render_to_host_async(ctx, tables, cube, C.byref(cam), C.byref(d), C.byref(shading),
+                                         out_host.data_ptr(), 1 if rgb else 0, _stream(stream), C.byref(t)))
+    return t.value
+
+
+def bh_host_wait(ctx, ticket: int) -> None:
+    """Block until frame `ticket` of bh_render_to_host_async is in host memory."""
+    _check(lib().bh_host_wait(ctx, C.c_ulonglong(ticket)))
 
 
 def _cams(cameras):

@@ -533,6 +533,12 @@ extern "C" void bh_destroy(bh_ctx *c) {
   if (c->cam_host) cudaFreeHost(c->cam_host);
   if (c->cam_dev) cudaFree(c->cam_dev);
   if (c->frame_dev) cudaFree(c->frame_dev);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ring_dev[k]) cudaFree(c->ring_dev[k]);
+    if (c->ring_ready[k]) cudaEventDestroy(c->ring_ready[k]);
+    if (c->ring_done[k]) cudaEventDestroy(c->ring_done[k]);
+  }
+  if (c->ring_copy) cudaStreamDestroy(c->ring_copy);
   if (c->bloom_dev) cudaFree(c->bloom_dev);
   if (c->bloom_bar) cudaFree(c->bloom_bar);
   if (c->orb_outs_host) cudaFreeHost(c->orb_outs_host);

@@ -118,6 +118,14 @@ struct bh_ctx {
   int orb_cap = 0;
   float *frame_dev = nullptr;         // bh_render_to_host frame buffer
   size_t frame_cap = 0;
+  // bh_render_to_host_async: two device frames; each is copied to the host
+  // on ring_copy while the next one renders
+  float *ring_dev[2] = {nullptr, nullptr};
+  size_t ring_cap = 0;
+  cudaStream_t ring_copy = nullptr;
+  cudaEvent_t ring_ready[2] = {nullptr, nullptr};  // the slot's last frame is rendered
+  cudaEvent_t ring_done[2] = {nullptr, nullptr};   // ... and its copy to the host has finished
+  unsigned long long ring_seq = 0;                 // frames issued (the next ticket)
   void *bloom_dev = nullptr;          // bh_bloom: mip pyramid scratch
   size_t bloom_cap = 0;
   unsigned *bloom_bar = nullptr;      // bh_bloom: grid-barrier counter

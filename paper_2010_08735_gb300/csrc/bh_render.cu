@@ -1409,6 +1409,94 @@ static bh_status render_to_host(bh_ctx *ctx, const bh_tables *t, const bh_cubema
   return BH_OK;
 }
 
+// Frames in flight: frame n renders into device slot n % 2 on the caller's
+// stream, then the copy engine moves it to the host on the context's copy
+// stream while frame n + 1 renders into the other slot.  A slot is rendered
+// into again only after its previous copy has finished (the stream waits on
+// that copy's event), so at most two frames are in flight and the rendering
+// of one overlaps the transfer of the other.
+static bh_status render_to_host_async(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                                      const bh_camera *cam, const bh_disc *disc, const bh_shading *sh,
+                                      float *host, void *stream, bool rgb, unsigned long long *ticket) {
+  if (!ctx || !host || !cam || !ticket) {
+    set_error("bh_render_to_host_async: NULL argument");
+    return BH_ERR_INVALID_ARG;
+  }
+  if (!validate_camera(cam, 0)) return BH_ERR_INVALID_ARG;
+  BH_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaPointerAttributes pa;
+  const bool pinned = cudaPointerGetAttributes(&pa, host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+  cudaGetLastError();  // pageable memory: cudaPointerGetAttributes may have set an error
+  if (!pinned) {
+    set_error("bh_render_to_host_async: the host buffer must be pinned (cudaHostAlloc or cudaHostRegister)");
+    return BH_ERR_INVALID_ARG;
+  }
+  const size_t bytes = (rgb ? 3 * sizeof(float) : sizeof(float4)) * (size_t)cam->width * cam->height;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->ring_copy) {
+    BH_CUDA(cudaStreamCreateWithFlags(&ctx->ring_copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      BH_CUDA(cudaEventCreateWithFlags(&ctx->ring_ready[k], cudaEventDisableTiming));
+      BH_CUDA(cudaEventCreateWithFlags(&ctx->ring_done[k], cudaEventDisableTiming));
+    }
+  }
+  if (bytes > ctx->ring_cap) {
+    // every earlier copy has finished, and with it the render it waited for
+    BH_CUDA(cudaStreamSynchronize(ctx->ring_copy));
+    for (int k = 0; k < 2; ++k) {
+      if (ctx->ring_dev[k]) cudaFree(ctx->ring_dev[k]);
+      ctx->ring_dev[k] = nullptr;
+    }
+    ctx->ring_cap = 0;
+    for (int k = 0; k < 2; ++k) BH_CUDA(cudaMalloc((void **)&ctx->ring_dev[k], bytes));
+    ctx->ring_cap = bytes;
+  }
+  const int k = (int)(ctx->ring_seq & 1u);
+  // the slot's previous frame must have left the device before it is
+  // overwritten (a no-op before the slot's first copy)
+  BH_CUDA(cudaStreamWaitEvent(s, ctx->ring_done[k], 0));
+  bh_status st = render_one(ctx, t, cube, cam, disc, sh, ctx->ring_dev[k], nullptr, s, rgb);
+  if (st) return st;
+  BH_CUDA(cudaEventRecord(ctx->ring_ready[k], s));
+  BH_CUDA(cudaStreamWaitEvent(ctx->ring_copy, ctx->ring_ready[k], 0));
+  BH_CUDA(cudaMemcpyAsync(host, ctx->ring_dev[k], bytes, cudaMemcpyDeviceToHost, ctx->ring_copy));
+  BH_CUDA(cudaEventRecord(ctx->ring_done[k], ctx->ring_copy));
+  *ticket = ctx->ring_seq++;
+  return BH_OK;
+}
+
+extern "C" bh_status bh_render_to_host_async(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
+                                             const bh_camera *cam, const bh_disc *disc,
+                                             const bh_shading *sh, float *host, int rgb, void *stream,
+                                             unsigned long long *ticket) {
+  TraceRange trace_("bh_render_to_host_async");
+  if (rgb != 0 && rgb != 1) {
+    set_error("bh_render_to_host_async: rgb = %d, must be 0 (RGBA) or 1 (packed RGB)", rgb);
+    return BH_ERR_INVALID_ARG;
+  }
+  return render_to_host_async(ctx, t, cube, cam, disc, sh, host, stream, rgb == 1, ticket);
+}
+
+extern "C" bh_status bh_host_wait(bh_ctx *ctx, unsigned long long ticket) {
+  TraceRange trace_("bh_host_wait");
+  if (!ctx) { set_error("bh_host_wait: NULL context"); return BH_ERR_INVALID_ARG; }
+  cudaEvent_t e;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ticket >= ctx->ring_seq) {
+      set_error("bh_host_wait: ticket %llu was never issued (%llu issued)", ticket, ctx->ring_seq);
+      return BH_ERR_INVALID_ARG;
+    }
+    // the slot's event belongs to this frame or to a later one; copies run in
+    // order on one stream, so either has finished only after this frame's
+    e = ctx->ring_done[ticket & 1u];
+  }
+  BH_CUDA(cudaSetDevice(ctx->device));
+  BH_CUDA(cudaEventSynchronize(e));
+  return BH_OK;
+}
+
 extern "C" bh_status bh_render_to_host(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *cube,
                                        const bh_camera *cam, const bh_disc *disc,
                                        const bh_shading *sh, float *host, void *stream) {

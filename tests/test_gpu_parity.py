@@ -553,6 +553,46 @@ def test_render_to_host_rgb_equals_device(ctx, gpu_tables, static_scene, W, H):
     assert np.array_equal(pageable, ref)
 
 
+def test_render_to_host_async_frames_in_flight(ctx, gpu_tables, static_scene):
+    """Two frames in flight: a sequence of frames of changing camera, sizes and
+    both layouts, each enqueued before the previous one is waited for, lands
+    in host memory equal to the device render of the same camera; tickets
+    count up; a ticket never issued and a pageable buffer are rejected."""
+    cube, _ = static_scene
+    sh = bh.make_shading(1.0, EXPOSURE_STARS)
+    frames = []
+    for k, (W, H, rgb) in enumerate([(80, 40, True), (96, 54, True), (97, 61, False), (80, 40, True),
+                                     (160, 90, True), (64, 48, False), (80, 40, True)]):
+        cam = synth.camera(10.0 + 0.5 * k, 80.0 - 2.0 * k, width=W, height=H)
+        dev = torch.zeros((H, W, 4), device="cuda")
+        bh.bh_render(ctx, gpu_tables, cube, cam, synth.disc(), sh, dev)
+        torch.cuda.synchronize()
+        ref = dev.cpu().numpy()
+        frames.append((cam, rgb, ref[..., :3] if rgb else ref))
+    hosts = [torch.full((90, 160, 4), -1.0, dtype=torch.float32).pin_memory() for _ in range(2)]
+    prev, got = None, []
+    for k, (cam, rgb, ref) in enumerate(frames):
+        ch = 3 if rgb else 4
+        buf = hosts[k & 1].view(-1)[:cam["height"] * cam["width"] * ch].view(cam["height"], cam["width"], ch)
+        buf.fill_(-1.0)
+        tk = bh.bh_render_to_host_async(ctx, gpu_tables, cube, cam, synth.disc(), sh, buf, rgb)
+        if prev is not None:
+            assert tk == prev[0] + 1
+            bh.bh_host_wait(ctx, prev[0])
+            got.append(prev[1].numpy().copy())
+        prev = (tk, buf)
+    bh.bh_host_wait(ctx, prev[0])
+    got.append(prev[1].numpy().copy())
+    for (cam, rgb, ref), img in zip(frames, got):
+        assert np.array_equal(img, ref)
+    with pytest.raises(bh.BhError):
+        bh.bh_host_wait(ctx, prev[0] + 1)
+    cam = frames[0][0]
+    pageable = torch.zeros((cam["height"], cam["width"], 3), dtype=torch.float32)
+    with pytest.raises(bh.BhError):
+        bh.bh_render_to_host_async(ctx, gpu_tables, cube, cam, synth.disc(), sh, pageable, True)
+
+
 def test_serve_results_equal_alone(ctx, gpu_tables, static_scene):
     """Continuous batching: frames submitted while others are in flight come
     out equal to the same frame rendered alone."""
