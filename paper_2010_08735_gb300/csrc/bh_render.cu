@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "bh_internal.cuh"
 
@@ -621,6 +622,8 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           // star at (ii + (ps + 1/2)/256, jj + (pt + 1/2)/256) in level-L texels
           const float q11 = i11 * (1.f / 256.f), q12 = i12 * (1.f / 256.f);
           const float q21 = i21 * (1.f / 256.f), q22 = i22 * (1.f / 256.f);
+          // (w, h) of a star as one packed f32x2 multiply-add chain per take
+          const float2 q1p = make_float2(q11, q21), q2p = make_float2(q12, q22), ip = make_float2(i11, i21);
           // One footprint row at a time: the row's occupancy bits select the
           // texels that hold stars; only those records are read.
           const int nrow = i1 - i0 + 1;
@@ -636,49 +639,59 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
             const unsigned lo = __ldg(mrow), hi = straddle ? __ldg(mrow + 1) : 0u;
             return __funnelshift_r(lo, hi, b0) & rowbits;  // bits b0.. of the 64-bit window
           };
-          const bool bf16 = P.cube_bf16;
-          unsigned bits = j0 <= j1 ? row_bits(j0) : 0u;
-          for (int jj = j0; jj <= j1; ++jj) {
-            // the next row's occupancy is requested before this row's records
-            const unsigned nbits = jj < j1 ? row_bits(jj + 1) : 0u;
-            if (nrow > 0) visited += nrow;
-            const float dt = (jj - cT) + 0.5f / 256.f;
-            const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
-            const uint2 *rowp = rec + (jj * NL + i0);
-            // the stars of this row: texel i0 + k for every occupied k
-            while (bits) {
-              const int k = __ffs(bits) - 1;
-              bits &= bits - 1u;
-              if (!check(jj >= 0 && jj < NL && i0 + k >= 0 && i0 + k < NL)) continue;
-              const uint2 r = __ldg(rowp + k);
-              const unsigned pw = r.y >> 16;
-              const float ps = byte_to_float(pw & 255u), pt = byte_to_float(pw >> 8);
-              const float w = fmaf(q11, ps, fmaf(q12, pt, fmaf(i11, (float)k, wrow)));
-              const float h = fmaf(q21, ps, fmaf(q22, pt, fmaf(i21, (float)k, hrow)));
-              // tent weight f(w) f(h), 0 outside the footprint
-              const float wt = fmaxf(1.f - fabsf(w), 0.f) * fmaxf(1.f - fabsf(h), 0.f);
-              float X, Y, Z;
-              if (bf16) {
-                X = __uint_as_float(r.x << 16);
-                Y = __uint_as_float(r.x & 0xffff0000u);
-                Z = __uint_as_float(r.y << 16);
-              } else {
-                __half2 xy2, zp2;
-                memcpy(&xy2, &r.x, 4);
-                memcpy(&zp2, &r.y, 4);
-                const float2 xy = __half22float2(xy2);
-                X = xy.x;
-                Y = xy.y;
-                Z = __low2float(zp2);
+          // the loop is compiled once per record format (no format test per star)
+          auto gather = [&](auto bf16_tag) {
+            unsigned bits = j0 <= j1 ? row_bits(j0) : 0u;
+            for (int jj = j0; jj <= j1; ++jj) {
+              // the next row's occupancy is requested before this row's records
+              const unsigned nbits = jj < j1 ? row_bits(jj + 1) : 0u;
+              if (nrow > 0) visited += nrow;
+              const float dt = (jj - cT) + 0.5f / 256.f;
+              const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
+              const uint2 *rowp = rec + (jj * NL + i0);
+              // the stars of this row: texel i0 + k for every occupied k
+              while (bits) {
+                const int k = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                if (!check(jj >= 0 && jj < NL && i0 + k >= 0 && i0 + k < NL)) continue;
+                const uint2 r = __ldg(rowp + k);
+                // the star's position bytes (bits 16..23 and 24..31 of r.y) as floats
+                const float ps = __uint_as_float(__byte_perm(r.y, 0x4B000000u, 0x7442u)) - 8388608.f;
+                const float pt = __uint_as_float(__byte_perm(r.y, 0x4B000000u, 0x7443u)) - 8388608.f;
+                const float kf = byte_to_float((unsigned)k);
+                // w = q11 ps + (q12 pt + (i11 k + wrow)), h likewise: each half
+                // rounds exactly as the scalar fmaf chain would
+                const float2 wh = __ffma2_rn(q1p, make_float2(ps, ps), __ffma2_rn(q2p, make_float2(pt, pt),
+                                    __ffma2_rn(ip, make_float2(kf, kf), make_float2(wrow, hrow))));
+                const float w = wh.x, h = wh.y;
+                // tent weight f(w) f(h), 0 outside the footprint
+                const float wt = fmaxf(1.f - fabsf(w), 0.f) * fmaxf(1.f - fabsf(h), 0.f);
+                float X, Y, Z;
+                if constexpr (decltype(bf16_tag)::value) {
+                  X = __uint_as_float(r.x << 16);
+                  Y = __uint_as_float(r.x & 0xffff0000u);
+                  Z = __uint_as_float(r.y << 16);
+                } else {
+                  __half2 xy2, zp2;
+                  memcpy(&xy2, &r.x, 4);
+                  memcpy(&zp2, &r.y, 4);
+                  const float2 xy = __half22float2(xy2);
+                  X = xy.x;
+                  Y = xy.y;
+                  Z = __low2float(zp2);
+                }
+                // the level's scale 4^L multiplies the sums once, after the loop
+                // (a power of two: the same result as scaling every weight);
+                // X and Y accumulate as one f32x2 pair
+                const float2 sxy = __ffma2_rn(make_float2(wt, wt), make_float2(X, Y), make_float2(SX, SY));
+                SX = sxy.x;
+                SY = sxy.y;
+                SZ = fmaf(wt, Z, SZ);
               }
-              // the level's scale 4^L multiplies the sums once, after the loop
-              // (a power of two: the same result as scaling every weight)
-              SX = fmaf(wt, X, SX);
-              SY = fmaf(wt, Y, SY);
-              SZ = fmaf(wt, Z, SZ);
+              bits = nbits;
             }
-            bits = nbits;
-          }
+          };
+          if (P.cube_bf16) gather(std::true_type{}); else gather(std::false_type{});
           SX *= lscale;
           SY *= lscale;
           SZ *= lscale;
