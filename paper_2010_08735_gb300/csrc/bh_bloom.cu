@@ -41,7 +41,17 @@ constexpr int kBloomTile = 64;                      // output texels per tile si
 constexpr int kBloomHalo = 3;                       // blur radius
 constexpr int kBloomSpan = kBloomTile + 2 * kBloomHalo;
 constexpr int kBloomThreads = 1024;
-constexpr size_t kBloomSmem = sizeof(float4) * (kBloomSpan * kBloomSpan + kBloomSpan * kBloomTile);
+// composite tiles: per level at most ceil((kCompH - 1) 2^-k) + 2 staged texel rows of kCompW entries
+constexpr int kCompW = 256, kCompH = 32;
+constexpr int comp_rows() {
+  int n = 0;
+  for (int k = 1; k <= kBloomMaxLevels; ++k) n += ((kCompH - 1) + (1 << k) - 1) / (1 << k) + 2;
+  return n;
+}
+constexpr size_t kBlurSmem = sizeof(float4) * (kBloomSpan * kBloomSpan + kBloomSpan * kBloomTile);
+constexpr size_t kCompSmem = sizeof(float4) * kCompW * comp_rows();
+constexpr size_t kBloomSmem = kBlurSmem > kCompSmem ? kBlurSmem : kCompSmem;
+static_assert(kBloomSmem <= 227 * 1024, "bloom shared memory");
 
 struct BloomParams {
   const float4 *in;
@@ -87,6 +97,20 @@ __device__ bool grid_barrier(const BloomParams &P, unsigned phase) {
   }
   __syncthreads();
   return ok != 0;
+}
+
+// Pull the frame rows of composite tile `tile` into L2 (one bulk prefetch per
+// pixel row, issued by the lanes of warp 0): the composite of that tile then
+// finds them there.  Rows start 16-byte aligned and span whole pixels.
+__device__ __forceinline__ void prefetch_comp_tile(const BloomParams &P, int tile, int kw, int kh) {
+  const int W = P.w[0], H = P.h[0];
+  const int tcx = (W + kw - 1) / kw, ntiles = tcx * ((H + kh - 1) / kh);
+  if (threadIdx.x >= 32 || tile >= ntiles) return;
+  const int X0 = (tile % tcx) * kw, y = (tile / tcx) * kh + (int)threadIdx.x;
+  if ((int)threadIdx.x >= kh || y >= H) return;
+  const float4 *src = P.in + ((size_t)y * W + X0);
+  const unsigned bytes = (unsigned)(sizeof(float4) * min(kw, W - X0));
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Box level k at texel (x, y), indices clamped to level k, from level k-1.
@@ -167,6 +191,7 @@ __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams 
   float4 *sD = sb;                              // kBloomSpan x kBloomSpan box texels
   float4 *sH = sb + kBloomSpan * kBloomSpan;    // kBloomSpan rows x kBloomTile: blurred along x
   unsigned phase = 0;
+  prefetch_comp_tile(P, blockIdx.x, kCompW, kCompH);  // read after the pyramid is built
   if (P.n > 0) {
     // ---- box levels 1..6 by regions (ping-pong halves of the shared buffer)
     const int nr = min(P.n, kBloomRegionLevels);
@@ -227,42 +252,64 @@ __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams 
     }
     if (!grid_barrier(P, ++phase)) return;
   }
-  // composite at full resolution, two pixels per thread and iteration (their
-  // loads in flight together)
+  // composite at full resolution, by tiles of kCompW x kCompH pixels.  The
+  // bilinear lookup of level k at pixel (x, y) is a lerp along v of two
+  // lerps along u; the lerps along u depend only on the pixel's column and
+  // the texel row, so for each level the tile's texel rows are first
+  // interpolated along u at every pixel column of the tile and staged in
+  // shared memory (hrow), and each pixel then takes one lerp along v per
+  // level from two staged values.  The arithmetic per pixel is exactly that
+  // of interpolating alone.
   const int W = P.w[0], H = P.h[0];
-  const long long npx = (long long)W * H, stride = (long long)gridDim.x * blockDim.x;
-  auto composite = [&](long long p, float4 &res) {
-    const int y = (int)(p / W), x = (int)(p - (long long)y * W);
-    const float4 c = P.in[p];
-    float r = P.wt[0] * c.x, g = P.wt[0] * c.y, b = P.wt[0] * c.z;
+  const int tcx = (W + kCompW - 1) / kCompW, ntiles = tcx * ((H + kCompH - 1) / kCompH);
+  float4 *hrow = sb;
+  __shared__ int s_base[kBloomMaxLevels + 1];  // per level: staged index of texel row 0 (off - jb)
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int X0 = (tile % tcx) * kCompW, Y0 = (tile / tcx) * kCompH;
+    __syncthreads();  // the previous tile's staged rows have been read
+    prefetch_comp_tile(P, tile + gridDim.x, kCompW, kCompH);
+    int off = 0;
     for (int k = 1; k <= P.n; ++k) {
-      const float s = 1.f / (float)(1 << k);
-      const float u = fmaf((float)x + 0.5f, s, -0.5f), v = fmaf((float)y + 0.5f, s, -0.5f);
-      const float fu = floorf(u), fv = floorf(v);
-      const float tu = u - fu, tv = v - fv;
+      const float s = __int_as_float((127 - k) << 23);  // 2^-k
       const int w = P.w[k], h = P.h[k];
-      const int i0 = min(max((int)fu, 0), w - 1), i1 = min(max((int)fu + 1, 0), w - 1);
-      const int j0 = min(max((int)fv, 0), h - 1), j1 = min(max((int)fv + 1, 0), h - 1);
-      const float4 *q = P.B[k];
-      const float4 a = q[(size_t)j0 * w + i0], bb = q[(size_t)j0 * w + i1];
-      const float4 cc = q[(size_t)j1 * w + i0], d = q[(size_t)j1 * w + i1];
-      const float wk = P.wt[k];
-      const float lr = fmaf(tv, fmaf(tu, d.x - cc.x, cc.x) - fmaf(tu, bb.x - a.x, a.x), fmaf(tu, bb.x - a.x, a.x));
-      const float lg = fmaf(tv, fmaf(tu, d.y - cc.y, cc.y) - fmaf(tu, bb.y - a.y, a.y), fmaf(tu, bb.y - a.y, a.y));
-      const float lb = fmaf(tv, fmaf(tu, d.z - cc.z, cc.z) - fmaf(tu, bb.z - a.z, a.z), fmaf(tu, bb.z - a.z, a.z));
-      r = fmaf(wk, lr, r);
-      g = fmaf(wk, lg, g);
-      b = fmaf(wk, lb, b);
+      // texel rows jb .. jb + nr - 1 (contents clamped) serve the tile's pixel rows
+      const int jb = (int)floorf(fmaf((float)Y0 + 0.5f, s, -0.5f));
+      const int nr = (int)floorf(fmaf((float)(Y0 + kCompH - 1) + 0.5f, s, -0.5f)) - jb + 2;
+      if (threadIdx.x == 0) s_base[k] = off - jb;
+      const float4 *Bk = P.B[k];
+      for (int e = threadIdx.x; e < nr * kCompW; e += blockDim.x) {
+        const int r = e / kCompW, c = e - r * kCompW;
+        const float u = fmaf((float)(X0 + c) + 0.5f, s, -0.5f);
+        const float fu = floorf(u), tu = u - fu;
+        const int i0 = min(max((int)fu, 0), w - 1), i1 = min(max((int)fu + 1, 0), w - 1);
+        const float4 *row = Bk + (size_t)min(max(jb + r, 0), h - 1) * w;
+        const float4 a = row[i0], b = row[i1];
+        hrow[(off + r) * kCompW + c] =
+            make_float4(fmaf(tu, b.x - a.x, a.x), fmaf(tu, b.y - a.y, a.y), fmaf(tu, b.z - a.z, a.z), 0.f);
+      }
+      off += nr;
     }
-    res = make_float4(r, g, b, 1.f);
-  };
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += 2 * stride) {
-    float4 r0, r1;
-    const bool two = p + stride < npx;
-    composite(p, r0);
-    if (two) composite(p + stride, r1);
-    P.out[p] = r0;
-    if (two) P.out[p + stride] = r1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kCompW * kCompH; e += blockDim.x) {
+      const int yy = e / kCompW, c = e - yy * kCompW;
+      const int x = X0 + c, y = Y0 + yy;
+      if (x >= W || y >= H) continue;
+      const long long p = (long long)y * W + x;
+      const float4 cp = P.in[p];
+      float r = P.wt[0] * cp.x, g = P.wt[0] * cp.y, b = P.wt[0] * cp.z;
+      for (int k = 1; k <= P.n; ++k) {
+        const float s = __int_as_float((127 - k) << 23);  // 2^-k
+        const float v = fmaf((float)y + 0.5f, s, -0.5f);
+        const float fv = floorf(v), tv = v - fv;
+        const int ri = s_base[k] + (int)fv;
+        const float4 h0 = hrow[ri * kCompW + c], h1 = hrow[(ri + 1) * kCompW + c];
+        const float wk = P.wt[k];
+        r = fmaf(wk, fmaf(tv, h1.x - h0.x, h0.x), r);
+        g = fmaf(wk, fmaf(tv, h1.y - h0.y, h0.y), g);
+        b = fmaf(wk, fmaf(tv, h1.z - h0.z, h0.z), b);
+      }
+      P.out[p] = make_float4(r, g, b, 1.f);
+    }
   }
 }
 
