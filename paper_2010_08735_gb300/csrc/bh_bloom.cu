@@ -48,10 +48,16 @@ constexpr int comp_rows() {
   for (int k = 1; k <= kBloomMaxLevels; ++k) n += ((kCompH - 1) + (1 << k) - 1) / (1 << k) + 2;
   return n;
 }
-constexpr size_t kBlurSmem = sizeof(float4) * (kBloomSpan * kBloomSpan + kBloomSpan * kBloomTile);
+// shared-memory row strides, padded so that lanes on consecutive rows of sD
+// or sH address distinct 16-byte bank groups
+constexpr int kSDStride = kBloomSpan + 1, kSHStride = kBloomTile + 1;
+constexpr int kBlurRun = 8;  // consecutive outputs per thread in each blur pass (a sliding window of taps)
+constexpr size_t kBlurSmem = sizeof(float4) * (kBloomSpan * kSDStride + kBloomSpan * kSHStride);
 constexpr size_t kCompSmem = sizeof(float4) * kCompW * comp_rows();
 constexpr size_t kBloomSmem = kBlurSmem > kCompSmem ? kBlurSmem : kCompSmem;
-static_assert(kBloomSmem <= 227 * 1024, "bloom shared memory");
+// with the composite's per-row tables (2 x kCompH x kBloomMaxLevels words) and
+// the barrier flag in static shared memory
+static_assert(kBloomSmem + 2 * 4 * kCompH * kBloomMaxLevels + 16 <= 227 * 1024, "bloom shared memory");
 
 struct BloomParams {
   const float4 *in;
@@ -61,7 +67,7 @@ struct BloomParams {
   int w[kBloomMaxLevels + 1], h[kBloomMaxLevels + 1];
   float wt[kBloomMaxLevels + 1];
   int n;
-  unsigned *bar;        // grid-barrier arrival counter (zero at launch)
+  unsigned *bar;        // [0] grid-barrier arrivals, [1] blocks done (both zero at launch)
   unsigned *status;
   unsigned long long wait_ns;
   int inject;           // fault injection: block 0 never arrives at the first barrier
@@ -113,6 +119,23 @@ __device__ __forceinline__ void prefetch_comp_tile(const BloomParams &P, int til
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// Pull the frame rows that region `reg` reads (its level-1 texels with their
+// 3-texel halo: 140 x 140 pixels, clamped to the frame) into L2, one bulk
+// prefetch per pixel row.
+__device__ __forceinline__ void prefetch_region(const BloomParams &P, int reg) {
+  const int W = P.w[0], H = P.h[0];
+  const int rx = (P.w[1] + kBloomTile - 1) / kBloomTile, regions = rx * ((P.h[1] + kBloomTile - 1) / kBloomTile);
+  constexpr int kRows = 2 * kBloomSpan;
+  if (reg >= regions || (int)threadIdx.x >= kRows) return;
+  const int gx = reg % rx, gy = reg / rx;
+  const int y = 2 * (gy * kBloomTile - kBloomHalo) + (int)threadIdx.x;
+  const int xa = max(2 * (gx * kBloomTile - kBloomHalo), 0), xb = min(2 * (gx * kBloomTile + kBloomTile + kBloomHalo), W);
+  if (y < 0 || y >= H || xa >= xb) return;
+  const float4 *src = P.in + ((size_t)y * W + xa);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((unsigned)(sizeof(float4) * (xb - xa)))
+               : "memory");
+}
+
 // Box level k at texel (x, y), indices clamped to level k, from level k-1.
 __device__ __forceinline__ float4 box_texel(const BloomParams &P, int k, int x, int y) {
   x = min(max(x, 0), P.w[k] - 1);
@@ -134,50 +157,82 @@ __device__ __forceinline__ float4 box_texel(const BloomParams &P, int k, int x, 
 // reduces a region level by level in shared memory with no grid barrier.
 constexpr int kBloomRegionLevels = 7;
 
-// Blur (7 taps along x, then along y, clamped) of one 64x64 tile of level k,
-// its box texels read from global memory with a 3-texel halo.
+// Blur (7 taps along x, then along y, clamped) of one 64x64 tile of level k
+// whose box texels, with a 3-texel halo at clamped coordinates, are in sD.
+__device__ void blur_staged(const BloomParams &P, int k, int x0, int y0, const float4 *sD, float4 *sH);
+
+// The same, the box texels read from level k in global memory.
 __device__ void blur_tile(const BloomParams &P, int k, int x0, int y0, float4 *sD, float4 *sH) {
   const int w = P.w[k], h = P.h[k];
   const float4 *Dk = P.D[k];
   for (int i = threadIdx.x; i < kBloomSpan * kBloomSpan; i += blockDim.x) {
     const int r = i / kBloomSpan, c = i - r * kBloomSpan;
     const int x = min(max(x0 + c - kBloomHalo, 0), w - 1), y = min(max(y0 + r - kBloomHalo, 0), h - 1);
-    sD[i] = Dk[(size_t)y * w + x];
+    sD[r * kSDStride + c] = Dk[(size_t)y * w + x];
+  }
+  blur_staged(P, k, x0, y0, sD, sH);
+}
+
+__device__ void blur_staged(const BloomParams &P, int k, int x0, int y0, const float4 *sD, float4 *sH) {
+  const int w = P.w[k], h = P.h[k];
+  // Slot (r, c) of sD holds the texel at the clamped coordinates (x0 + c - 3,
+  // y0 + r - 3), so a tap past the level's edge finds the clamped texel in its
+  // own slot.  Each pass gives a thread kBlurRun consecutive outputs: it
+  // streams their kBlurRun + 6 texels once, in order, each into the sums of
+  // the outputs it is a tap of, so every output still sums its seven taps
+  // from -3 to 3.
+  __syncthreads();
+  constexpr int kWin = kBlurRun + 2 * kBloomHalo;
+  constexpr int kXItems = kBloomSpan * (kBloomTile / kBlurRun);
+  for (int it = threadIdx.x; it < kXItems; it += blockDim.x) {
+    const int r = it % kBloomSpan, c0 = (it / kBloomSpan) * kBlurRun;  // lanes on consecutive rows
+    float3 acc[kBlurRun];
+#pragma unroll
+    for (int o = 0; o < kBlurRun; ++o) acc[o] = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) {
+      const float4 v = sD[r * kSDStride + c0 + j];
+#pragma unroll
+      for (int o = 0; o < kBlurRun; ++o) {
+        const int t = j - o - kBloomHalo;  // this texel is tap t of output o
+        if (t >= -kBloomHalo && t <= kBloomHalo) {
+          const float kt = cBloomTaps[t < 0 ? -t : t];
+          acc[o].x = fmaf(kt, v.x, acc[o].x);
+          acc[o].y = fmaf(kt, v.y, acc[o].y);
+          acc[o].z = fmaf(kt, v.z, acc[o].z);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kBlurRun; ++o) sH[r * kSHStride + c0 + o] = make_float4(acc[o].x, acc[o].y, acc[o].z, 1.f);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kBloomSpan * kBloomTile; i += blockDim.x) {
-    const int r = i / kBloomTile, c = i - r * kBloomTile;
-    // taps past the level's edge read the clamped texel (the halo holds it
-    // only where the level continues)
+  constexpr int kYItems = kBloomTile * (kBloomTile / kBlurRun);
+  for (int it = threadIdx.x; it < kYItems; it += blockDim.x) {
+    const int c = it % kBloomTile, r0 = (it / kBloomTile) * kBlurRun;  // lanes on consecutive columns
+    float3 acc[kBlurRun];
+#pragma unroll
+    for (int o = 0; o < kBlurRun; ++o) acc[o] = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kWin; ++j) {
+      const float4 v = sH[(r0 + j) * kSHStride + c];
+#pragma unroll
+      for (int o = 0; o < kBlurRun; ++o) {
+        const int t = j - o - kBloomHalo;
+        if (t >= -kBloomHalo && t <= kBloomHalo) {
+          const float kt = cBloomTaps[t < 0 ? -t : t];
+          acc[o].x = fmaf(kt, v.x, acc[o].x);
+          acc[o].y = fmaf(kt, v.y, acc[o].y);
+          acc[o].z = fmaf(kt, v.z, acc[o].z);
+        }
+      }
+    }
     const int x = x0 + c;
-    float rr = 0.f, gg = 0.f, bb = 0.f;
 #pragma unroll
-    for (int t = -3; t <= 3; ++t) {
-      const int xx = min(max(x + t, 0), w - 1) - x0 + kBloomHalo;
-      const float4 v = sD[r * kBloomSpan + xx];
-      const float kt = cBloomTaps[t < 0 ? -t : t];
-      rr = fmaf(kt, v.x, rr);
-      gg = fmaf(kt, v.y, gg);
-      bb = fmaf(kt, v.z, bb);
+    for (int o = 0; o < kBlurRun; ++o) {
+      const int y = y0 + r0 + o;
+      if (x < w && y < h) P.B[k][(size_t)y * w + x] = make_float4(acc[o].x, acc[o].y, acc[o].z, 1.f);
     }
-    sH[i] = make_float4(rr, gg, bb, 1.f);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kBloomTile * kBloomTile; i += blockDim.x) {
-    const int r = i / kBloomTile, c = i - r * kBloomTile;
-    const int x = x0 + c, y = y0 + r;
-    if (x >= w || y >= h) continue;
-    float rr = 0.f, gg = 0.f, bb = 0.f;
-#pragma unroll
-    for (int t = -3; t <= 3; ++t) {
-      const int yy = min(max(y + t, 0), h - 1) - y0 + kBloomHalo;
-      const float4 v = sH[yy * kBloomTile + c];
-      const float kt = cBloomTaps[t < 0 ? -t : t];
-      rr = fmaf(kt, v.x, rr);
-      gg = fmaf(kt, v.y, gg);
-      bb = fmaf(kt, v.z, bb);
-    }
-    P.B[k][(size_t)y * w + x] = make_float4(rr, gg, bb, 1.f);
   }
   __syncthreads();
 }
@@ -186,48 +241,83 @@ __device__ void blur_tile(const BloomParams &P, int k, int x0, int y0, float4 *s
 // barriers: the box levels (regions of the frame reduced in shared memory;
 // levels past the seventh one grid-wide pass each), the blur of every tile of
 // every level, then the composite of every pixel.
+__device__ void bloom_body(const BloomParams &P);
+
+// The kernel proper, then its exit: the last block to leave (every block
+// leaves, barrier timeouts included) re-arms both counters for the next
+// launch, so no launch needs a reset of its own.
 __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams P) {
+  bloom_body(P);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(P.bar + 1, 1u) == gridDim.x - 1u) {
+      atomicExch(P.bar, 0u);
+      atomicExch(P.bar + 1, 0u);
+    }
+  }
+}
+
+__device__ void bloom_body(const BloomParams &P) {
   extern __shared__ float4 sb[];
-  float4 *sD = sb;                              // kBloomSpan x kBloomSpan box texels
-  float4 *sH = sb + kBloomSpan * kBloomSpan;    // kBloomSpan rows x kBloomTile: blurred along x
+  float4 *sD = sb;                              // kBloomSpan x kBloomSpan box texels (row stride kSDStride)
+  float4 *sH = sb + kBloomSpan * kSDStride;     // kBloomSpan rows x kBloomTile blurred along x (stride kSHStride)
   unsigned phase = 0;
+  if (P.n > 0) prefetch_region(P, blockIdx.x);        // read at once
   prefetch_comp_tile(P, blockIdx.x, kCompW, kCompH);  // read after the pyramid is built
   if (P.n > 0) {
-    // ---- box levels 1..6 by regions (ping-pong halves of the shared buffer)
+    // ---- box levels 1..7 by regions.  Level 1 of a region (64 x 64 texels)
+    // is built with a 3-texel halo at clamped coordinates straight from the
+    // frame and blurred in place (its halo texels are those of the
+    // neighbouring regions, recomputed); levels 2.. are reduced from its
+    // interior in shared memory, alternately in sH and sD.
     const int nr = min(P.n, kBloomRegionLevels);
     const int rx = (P.w[1] + kBloomTile - 1) / kBloomTile, regions = rx * ((P.h[1] + kBloomTile - 1) / kBloomTile);
-    // level 1 fills the first kBloomTile^2 texels, level 2 the next quarter of that, and so on alternately
-    float4 *cur = sb + kBloomTile * kBloomTile, *nxt = sb;
     for (int reg = blockIdx.x; reg < regions; reg += gridDim.x) {
       const int gx = reg % rx, gy = reg / rx;
-      for (int k = 1; k <= nr; ++k) {
+      {
+        const int w = P.w[1], h = P.h[1];
+        if (reg + (int)gridDim.x < regions) prefetch_region(P, reg + gridDim.x);
+        constexpr int kIt = (kBloomSpan * kBloomSpan + kBloomThreads - 1) / kBloomThreads;
+#pragma unroll
+        for (int j = 0; j < kIt; ++j) {
+          const int i = threadIdx.x + j * kBloomThreads;
+          if (i < kBloomSpan * kBloomSpan) {
+            const int r = i / kBloomSpan, c = i - r * kBloomSpan;
+            const int x = min(max(gx * kBloomTile + c - kBloomHalo, 0), w - 1);
+            const int y = min(max(gy * kBloomTile + r - kBloomHalo, 0), h - 1);
+            sD[r * kSDStride + c] = box_texel(P, 1, x, y);
+          }
+        }
+        blur_staged(P, 1, gx * kBloomTile, gy * kBloomTile, sD, sH);  // ends with __syncthreads
+      }
+      // level k - 1 of the region: at src with row stride sstr (level 1: sD's interior)
+      const float4 *src = sD + kBloomHalo * kSDStride + kBloomHalo;
+      int sstr = kSDStride;
+      for (int k = 2; k <= nr; ++k) {
         const int side = kBloomTile >> (k - 1);  // texels of level k per region side
         const int w = P.w[k], h = P.h[k];
+        float4 *dst = (k & 1) ? sD : sH;
         for (int i = threadIdx.x; i < side * side; i += blockDim.x) {
           const int lx = i % side, ly = i / side;
           const int x = gx * side + lx, y = gy * side + ly;
           if (x >= w || y >= h) continue;
-          float4 v;
-          if (k == 1) {
-            v = box_texel(P, 1, x, y);
-          } else {
-            // children in the previous level's region buffer (side 2 * side)
-            const int pw = P.w[k - 1], ph = P.h[k - 1], ps = 2 * side;
-            const int cx0 = min(2 * x, pw - 1) - 2 * gx * side, cx1 = min(2 * x + 1, pw - 1) - 2 * gx * side;
-            const int cy0 = min(2 * y, ph - 1) - 2 * gy * side, cy1 = min(2 * y + 1, ph - 1) - 2 * gy * side;
-            const float4 a = cur[cy0 * ps + cx0], b = cur[cy0 * ps + cx1];
-            const float4 c = cur[cy1 * ps + cx0], d = cur[cy1 * ps + cx1];
-            v = make_float4(0.25f * ((a.x + b.x) + (c.x + d.x)), 0.25f * ((a.y + b.y) + (c.y + d.y)),
-                            0.25f * ((a.z + b.z) + (c.z + d.z)), 1.f);
-          }
-          nxt[i] = v;
+          // children in the previous level's region (side 2 * side)
+          const int pw = P.w[k - 1], ph = P.h[k - 1];
+          const int cx0 = min(2 * x, pw - 1) - 2 * gx * side, cx1 = min(2 * x + 1, pw - 1) - 2 * gx * side;
+          const int cy0 = min(2 * y, ph - 1) - 2 * gy * side, cy1 = min(2 * y + 1, ph - 1) - 2 * gy * side;
+          const float4 a = src[cy0 * sstr + cx0], b = src[cy0 * sstr + cx1];
+          const float4 c = src[cy1 * sstr + cx0], d = src[cy1 * sstr + cx1];
+          const float4 v = make_float4(0.25f * ((a.x + b.x) + (c.x + d.x)), 0.25f * ((a.y + b.y) + (c.y + d.y)),
+                                       0.25f * ((a.z + b.z) + (c.z + d.z)), 1.f);
+          dst[i] = v;
           P.D[k][(size_t)y * w + x] = v;
         }
         __syncthreads();
-        float4 *t = cur;
-        cur = nxt;
-        nxt = t;
+        src = dst;
+        sstr = side;
       }
+      __syncthreads();  // the region's shared buffers are free for the next one
     }
     // ---- levels past the region's depth: one grid-wide pass each
     for (int k = kBloomRegionLevels + 1; k <= P.n; ++k) {
@@ -239,13 +329,13 @@ __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams 
       }
     }
     if (!grid_barrier(P, ++phase)) return;
-    // ---- blur every 64x64 tile of every level
+    // ---- blur every 64x64 tile of levels 2.. (level 1 was blurred by regions)
     int tiles_before[kBloomMaxLevels + 2];
-    tiles_before[1] = 0;
-    for (int k = 1; k <= P.n; ++k)
+    tiles_before[1] = tiles_before[2] = 0;
+    for (int k = 2; k <= P.n; ++k)
       tiles_before[k + 1] = tiles_before[k] + ((P.w[k] + kBloomTile - 1) / kBloomTile) * ((P.h[k] + kBloomTile - 1) / kBloomTile);
     for (int tile = blockIdx.x; tile < tiles_before[P.n + 1]; tile += gridDim.x) {
-      int k = 1;
+      int k = 2;
       while (tile >= tiles_before[k + 1]) ++k;
       const int t = tile - tiles_before[k], tx = (P.w[k] + kBloomTile - 1) / kBloomTile;
       blur_tile(P, k, (t % tx) * kBloomTile, (t / tx) * kBloomTile, sD, sH);
@@ -263,7 +353,11 @@ __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams 
   const int W = P.w[0], H = P.h[0];
   const int tcx = (W + kCompW - 1) / kCompW, ntiles = tcx * ((H + kCompH - 1) / kCompH);
   float4 *hrow = sb;
-  __shared__ int s_base[kBloomMaxLevels + 1];  // per level: staged index of texel row 0 (off - jb)
+  // per tile row and level: tv, and the staged index of the row's upper texel row
+  __shared__ float s_tv[kCompH][kBloomMaxLevels];  // [row][k - 1]
+  __shared__ int s_ri[kCompH][kBloomMaxLevels];
+  static_assert(kBloomThreads % kCompW == 0 && kBloomThreads / 32 == kCompH, "composite thread mapping");
+  const int cc = threadIdx.x % kCompW, rstep = kBloomThreads / kCompW;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int X0 = (tile % tcx) * kCompW, Y0 = (tile / tcx) * kCompH;
     __syncthreads();  // the previous tile's staged rows have been read
@@ -275,40 +369,46 @@ __global__ void __launch_bounds__(kBloomThreads) bloom_kernel(const BloomParams 
       // texel rows jb .. jb + nr - 1 (contents clamped) serve the tile's pixel rows
       const int jb = (int)floorf(fmaf((float)Y0 + 0.5f, s, -0.5f));
       const int nr = (int)floorf(fmaf((float)(Y0 + kCompH - 1) + 0.5f, s, -0.5f)) - jb + 2;
-      if (threadIdx.x == 0) s_base[k] = off - jb;
+      if ((int)threadIdx.x < kCompH) {
+        const float v = fmaf((float)(Y0 + (int)threadIdx.x) + 0.5f, s, -0.5f);
+        const float fv = floorf(v);
+        s_tv[threadIdx.x][k - 1] = v - fv;
+        s_ri[threadIdx.x][k - 1] = off + (int)fv - jb;
+      }
+      // this thread's column of the tile: its u, once per level
+      const float u = fmaf((float)(X0 + cc) + 0.5f, s, -0.5f);
+      const float fu = floorf(u), tu = u - fu;
+      const int i0 = min(max((int)fu, 0), w - 1), i1 = min(max((int)fu + 1, 0), w - 1);
       const float4 *Bk = P.B[k];
-      for (int e = threadIdx.x; e < nr * kCompW; e += blockDim.x) {
-        const int r = e / kCompW, c = e - r * kCompW;
-        const float u = fmaf((float)(X0 + c) + 0.5f, s, -0.5f);
-        const float fu = floorf(u), tu = u - fu;
-        const int i0 = min(max((int)fu, 0), w - 1), i1 = min(max((int)fu + 1, 0), w - 1);
+      for (int r = threadIdx.x / kCompW; r < nr; r += rstep) {
         const float4 *row = Bk + (size_t)min(max(jb + r, 0), h - 1) * w;
         const float4 a = row[i0], b = row[i1];
-        hrow[(off + r) * kCompW + c] =
+        hrow[(off + r) * kCompW + cc] =
             make_float4(fmaf(tu, b.x - a.x, a.x), fmaf(tu, b.y - a.y, a.y), fmaf(tu, b.z - a.z, a.z), 0.f);
       }
       off += nr;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kCompW * kCompH; e += blockDim.x) {
-      const int yy = e / kCompW, c = e - yy * kCompW;
-      const int x = X0 + c, y = Y0 + yy;
-      if (x >= W || y >= H) continue;
-      const long long p = (long long)y * W + x;
-      const float4 cp = P.in[p];
-      float r = P.wt[0] * cp.x, g = P.wt[0] * cp.y, b = P.wt[0] * cp.z;
-      for (int k = 1; k <= P.n; ++k) {
-        const float s = __int_as_float((127 - k) << 23);  // 2^-k
-        const float v = fmaf((float)y + 0.5f, s, -0.5f);
-        const float fv = floorf(v), tv = v - fv;
-        const int ri = s_base[k] + (int)fv;
-        const float4 h0 = hrow[ri * kCompW + c], h1 = hrow[(ri + 1) * kCompW + c];
-        const float wk = P.wt[k];
-        r = fmaf(wk, fmaf(tv, h1.x - h0.x, h0.x), r);
-        g = fmaf(wk, fmaf(tv, h1.y - h0.y, h0.y), g);
-        b = fmaf(wk, fmaf(tv, h1.z - h0.z, h0.z), b);
+    // warp yy takes tile row yy, its lanes every 32nd column
+    const int yy = threadIdx.x >> 5, y = Y0 + yy;
+    if (y < H) {
+      for (int c = threadIdx.x & 31; c < kCompW; c += 32) {
+        const int x = X0 + c;
+        if (x >= W) break;
+        const long long p = (long long)y * W + x;
+        const float4 cp = P.in[p];
+        float r = P.wt[0] * cp.x, g = P.wt[0] * cp.y, b = P.wt[0] * cp.z;
+        for (int k = 1; k <= P.n; ++k) {
+          const float tv = s_tv[yy][k - 1];
+          const int ri = s_ri[yy][k - 1];
+          const float4 h0 = hrow[ri * kCompW + c], h1 = hrow[(ri + 1) * kCompW + c];
+          const float wk = P.wt[k];
+          r = fmaf(wk, fmaf(tv, h1.x - h0.x, h0.x), r);
+          g = fmaf(wk, fmaf(tv, h1.y - h0.y, h0.y), g);
+          b = fmaf(wk, fmaf(tv, h1.z - h0.z, h0.z), b);
+        }
+        P.out[p] = make_float4(r, g, b, 1.f);
       }
-      P.out[p] = make_float4(r, g, b, 1.f);
     }
   }
 }
@@ -367,7 +467,11 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
     BH_CUDA(cudaMalloc((void **)&ctx->bloom_dev, need));
     ctx->bloom_cap = need;
   }
-  if (!ctx->bloom_bar) BH_CUDA(cudaMalloc((void **)&ctx->bloom_bar, sizeof(unsigned)));
+  if (!ctx->bloom_bar) {
+    // arrivals and blocks done: zero now; every launch leaves them zero again
+    BH_CUDA(cudaMalloc((void **)&ctx->bloom_bar, 2 * sizeof(unsigned)));
+    BH_CUDA(cudaMemsetAsync(ctx->bloom_bar, 0, 2 * sizeof(unsigned), s));
+  }
   static bool taps_ready[64] = {false};
   static int coop_blocks[64] = {0};
   if (ctx->device < 64 && !taps_ready[ctx->device]) {
@@ -413,7 +517,6 @@ extern "C" bh_status bh_bloom(bh_ctx *ctx, const float *in_device, float *out_de
     P.wait_ns = 2000000ull;  // 2 ms
     ctx->inject_bloom_barrier = 0;
   }
-  BH_CUDA(cudaMemsetAsync(ctx->bloom_bar, 0, sizeof(unsigned), s));
   void *args[] = {&P};
   BH_CUDA(cudaLaunchCooperativeKernel((const void *)bloom_kernel, dim3(coop_blocks[ctx->device]),
                                       dim3(kBloomThreads), args, kBloomSmem, s));
