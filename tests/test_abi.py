@@ -51,3 +51,23 @@ def test_cubemap_record_count(libbh):
 def test_last_error_without_gpu(libbh):
     libbh.bh_last_error.restype = ctypes.c_char_p
     assert libbh.bh_last_error() == b""
+
+
+def test_host_frame_calls_reject_bad_arguments_before_any_device_work(libbh):
+    """The two-frames-in-flight host path validates its arguments on the host:
+    a NULL context, a NULL ticket or an rgb flag other than 0/1 is an
+    argument error, reported without a CUDA call (so it holds with no GPU)."""
+    from paper_2010_08735_gb300 import bh
+    libbh.bh_last_error.restype = ctypes.c_char_p
+    libbh.bh_host_wait.argtypes = [ctypes.c_void_p, ctypes.c_ulonglong]
+    assert libbh.bh_host_wait(None, 0) == bh.BH_ERR_INVALID_ARG
+    assert b"NULL context" in libbh.bh_last_error()
+    vp = ctypes.c_void_p
+    libbh.bh_render_to_host_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int, vp, vp]
+    t = ctypes.c_ulonglong(0)
+    assert libbh.bh_render_to_host_async(None, None, None, None, None, None, None, 2, None,
+                                         ctypes.byref(t)) == bh.BH_ERR_INVALID_ARG
+    assert b"rgb = 2" in libbh.bh_last_error()
+    assert libbh.bh_render_to_host_async(None, None, None, None, None, None, None, 1, None,
+                                         ctypes.byref(t)) == bh.BH_ERR_INVALID_ARG
+    assert b"NULL argument" in libbh.bh_last_error()
