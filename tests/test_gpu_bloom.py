@@ -55,7 +55,11 @@ def test_weights_match_oracle():
         assert np.allclose(bh.bh_bloom_weights(fov, H, K), ob.bloom_weights(fov, H, K), rtol=1e-12, atol=1e-15)
 
 
-@pytest.mark.parametrize("H,W,K", [(256, 256, 6), (61, 97, 4), (1, 1, 2), (33, 17, 0), (1080, 1920, 6)])
+# (300, 520, 10): the maximum level count (levels 8..10 one grid-wide pass
+# each, the composite's staged rows at their largest); (129, 257, 8): odd
+# sizes at every level past the region depth
+@pytest.mark.parametrize("H,W,K", [(256, 256, 6), (61, 97, 4), (1, 1, 2), (33, 17, 0), (1080, 1920, 6),
+                                   (300, 520, 10), (129, 257, 8)])
 def test_bloom_matches_oracle(ctx, H, W, K):
     img = hdr_frame(H, W, seed=H * 7 + W)
     w = bh.bh_bloom_weights(math.radians(60), max(H, 2), K)
