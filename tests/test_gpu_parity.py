@@ -389,6 +389,9 @@ def test_render_hit_delays(ctx, orc, orc_tables_t, orc_colour, gpu_tables, uploa
     synth.camera(1.3, 30.0, v=(0.0, 0.4, 0.0), width=64, height=64),  # inside the photon sphere
     synth.camera(8.0, 10.0, width=3, height=1),
     synth.camera(8.0, 10.0, width=1, height=1),
+    synth.camera(6.0, 90.0, width=65, height=49),  # in the disc plane, inside the disc; odd sizes
+    synth.camera(1.02, 60.0, width=48, height=32),  # just outside the horizon
+    synth.camera(10.0, 80.0, v=(0.0, 0.0, 0.99), width=64, height=48),  # v = 0.99c
 ])
 def test_render_configs_small(ctx, orc, gpu_tables, static_scene, cam):
     cube, scene = static_scene
@@ -397,6 +400,22 @@ def test_render_configs_small(ctx, orc, gpu_tables, static_scene, cam):
                                           name=f"small_{cam['width']}x{cam['height']}_r{cam['r']}")
     check_stages(gd, od, mask)
     check_rgb(og, oo, od, mask, cam, "small")
+
+
+def test_empty_star_field_equals_no_cube_map(ctx, gpu_tables):
+    """A cube map built from no stars adds no light: the frame equals the one
+    rendered without a cube map, bit for bit, in the timed and debug forms."""
+    cube = bh.bh_build_star_cubemap(ctx, np.zeros((0, 5), dtype=np.float32), 256, 1)
+    try:
+        cam = synth.camera(6.0, 85.0, v=(0.0, 0.0, 0.5), width=96, height=54)
+        disc = synth.disc(3.0, 20.0)
+        with_cube, _ = gpu_render(ctx, gpu_tables, cube, cam, disc, debug=False)
+        without, _ = gpu_render(ctx, gpu_tables, None, cam, disc, debug=False)
+        assert np.array_equal(with_cube, without)
+        dbg_cube, _ = gpu_render(ctx, gpu_tables, cube, cam, disc)
+        assert np.array_equal(dbg_cube, without)
+    finally:
+        bh.bh_cubemap_free(cube)
 
 
 def test_star_centroids_sparse_field(ctx, orc, orc_tables, orc_colour, gpu_tables):
