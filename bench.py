@@ -125,17 +125,21 @@ def measured_peaks():
     return None
 
 
-def render_traffic():
-    """DRAM bytes per render launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    f = ROOT / "profiles" / "render_traffic.json"
+def kernel_traffic(record="render_traffic.json", source="bh_render.cu"):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    f = ROOT / "profiles" / record
     if not f.exists():
         return None
     d = json.loads(f.read_text())
-    src = (ROOT / "paper_2010_08735_gb300" / "csrc" / "bh_render.cu").read_bytes()
+    src = (ROOT / "paper_2010_08735_gb300" / "csrc" / source).read_bytes()
     if d.get("kernel_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return d.get("dram_bytes_per_launch")
+
+
+def render_traffic():
+    return kernel_traffic("render_traffic.json", "bh_render.cu")
 
 
 def work_counts(name):
@@ -459,7 +463,8 @@ def bloom_run(bh, ctx, out, W, H, fov_y, flush, stream, frames=400, levels=6):
     return {"ms_per_frame": ms, "frames_per_s": 1000.0 / ms, "levels": levels, "launches_per_frame": 1,
             "weights": [float(x) for x in w],
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "bytes_per_frame": nbytes}}
+                         "bytes_per_frame": nbytes,
+                         "traffic": kernel_traffic("bloom_traffic.json", "bh_bloom.cu")}}
 
 
 def run_ours(args):
