@@ -642,13 +642,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           // the loop is compiled once per record format (no format test per star)
           auto gather = [&](auto bf16_tag) {
             unsigned bits = j0 <= j1 ? row_bits(j0) : 0u;
-            for (int jj = j0; jj <= j1; ++jj) {
+            float jf = (float)j0;                   // jj as a float (exact)
+            const uint2 *rowp = rec + (j0 * NL + i0);  // texel i0 of row jj
+            for (int jj = j0; jj <= j1; ++jj, jf += 1.f, rowp += NL) {
               // the next row's occupancy is requested before this row's records
               const unsigned nbits = jj < j1 ? row_bits(jj + 1) : 0u;
               if (nrow > 0) visited += nrow;
-              const float dt = (jj - cT) + 0.5f / 256.f;
+              const float dt = (jf - cT) + 0.5f / 256.f;
               const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
-              const uint2 *rowp = rec + (jj * NL + i0);
               // the stars of this row: texel i0 + k for every occupied k
               while (bits) {
                 const int k = __ffs(bits) - 1;
