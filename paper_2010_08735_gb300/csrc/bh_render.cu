@@ -633,20 +633,22 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
           const int w0i = i0 >> 5, b0 = i0 & 31;
           const unsigned rowbits = nrow <= 0 ? 0u : nrow >= 32 ? 0xffffffffu : (1u << nrow) - 1u;
           const bool straddle = b0 + nrow > 32 && w0i + 1 < wpr;
-          auto row_bits = [&](const int jj) {
+          // the occupancy words of row jj at mrow (the row's word w0i)
+          auto row_bits = [&](const int jj, const unsigned *mrow) {
             if (!check(jj >= 0 && jj < NL && w0i >= 0 && w0i + (straddle ? 1 : 0) < wpr)) return 0u;
-            const unsigned *mrow = mrows + (jj * wpr + w0i);
             const unsigned lo = __ldg(mrow), hi = straddle ? __ldg(mrow + 1) : 0u;
             return __funnelshift_r(lo, hi, b0) & rowbits;  // bits b0.. of the 64-bit window
           };
           // the loop is compiled once per record format (no format test per star)
           auto gather = [&](auto bf16_tag) {
-            unsigned bits = j0 <= j1 ? row_bits(j0) : 0u;
+            const unsigned *mrow = mrows + (j0 * wpr + w0i);  // row jj's occupancy words
+            unsigned bits = j0 <= j1 ? row_bits(j0, mrow) : 0u;
             float jf = (float)j0;                   // jj as a float (exact)
             const uint2 *rowp = rec + (j0 * NL + i0);  // texel i0 of row jj
             for (int jj = j0; jj <= j1; ++jj, jf += 1.f, rowp += NL) {
               // the next row's occupancy is requested before this row's records
-              const unsigned nbits = jj < j1 ? row_bits(jj + 1) : 0u;
+              mrow += wpr;
+              const unsigned nbits = jj < j1 ? row_bits(jj + 1, mrow) : 0u;
               if (nrow > 0) visited += nrow;
               const float dt = (jf - cT) + 0.5f / 256.f;
               const float wrow = fmaf(i11, ds0, i12 * dt), hrow = fmaf(i21, ds0, i22 * dt);
