@@ -343,9 +343,11 @@ bh_status bh_render_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap
                           const bh_shading *shading, float *const *outs, void *stream);
 
 /* Autotuning of the batched launch: time the candidate launch shapes on the
- * given cameras (renders them several times, synchronously) and keep the
- * fastest for later bh_render_batch calls of this context.  *chosen receives
- * the chosen candidate index (may be NULL). */
+ * given cameras (renders them several times, synchronously, each timed run
+ * from a cold L2: a temporary scratch buffer of twice the L2 size is cleared
+ * before it; timed warm if that buffer cannot be allocated) and keep the
+ * shape with the smallest median time for later bh_render_batch calls of this
+ * context.  *chosen receives the chosen candidate index (may be NULL). */
 bh_status bh_autotune_batch(bh_ctx *ctx, const bh_tables *tables, const bh_cubemap *cubemap,
                             int n, const bh_camera *cameras, const bh_disc *disc,
                             const bh_shading *shading, float *const *outs, int *chosen);
