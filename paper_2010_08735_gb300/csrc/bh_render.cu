@@ -54,6 +54,7 @@ struct RenderParams {
   int d_n;
   const void *U;
   int u_ne, u_nphi, u_bytes;
+  float d_n1f, u_ne1f, u_nphi1f;  // d_n - 1, u_ne - 1, u_nphi - 1 as floats (operands, not conversions)
   const float *DTt, *UTt;   // regularised-time channels of D and U (debug and animated disc)
   const double *parts;      // animated disc: 8 doubles per particle (u1, u2, phi0, omega, c, rmin, rmax, 0)
   int n_parts;              // 0: constant disc density
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
     } else {
       int s = udot > 0.f ? 1 : -1;
       float xd = d_x(e2, em);
-      float fx = xd * (dn - 1);
+      float fx = xd * P.d_n1f;
       int xlo = em < 0.f ? 0 : n_half, xhi = em < 0.f ? n_half - 1 : dn - 1;
       float ua = 0.f, Dl, Da = 0.f, phia = INFINITY, yv;
       if (em < 0.f) {
@@ -406,14 +407,14 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float g = fmaf(-u, u, fmaf(-ua, u, fmaf(-ua, ua, ua + u)));
         float om = g > 0.f ? udot * udot / (ua * g) : 1.f - u / ua;
         yv = 1.f - sqrtf(fmaxf(om, 0.f));
-        Dl = d_bilinear_pair(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
-        Da = d_bilinear_pair(D, dn, fx, (float)(dn - 1), xlo, xhi, chk);
+        Dl = d_bilinear_pair(D, dn, fx, yv * P.d_n1f, xlo, xhi, chk);
+        Da = d_bilinear_pair(D, dn, fx, P.d_n1f, xlo, xhi, chk);
         phia = Da + 0.5f * kPiF;
       } else {
         const float r23 = 0.81649658f, r13 = 0.57735027f;
         float sq = sqrtf(fabsf(um));
         yv = (r23 + (um >= 0.f ? sq : -sq)) / (r23 + r13);
-        Dl = d_bilinear_pair(D, dn, fx, yv * (dn - 1), xlo, xhi, chk);
+        Dl = d_bilinear_pair(D, dn, fx, yv * P.d_n1f, xlo, xhi, chk);
       }
       if (alpha_ok && P.disc_on) {
         // Appendix A coordinates of U: x = 1/(1 + 6e^2), y = phi (1 + 6e^3)/(3 (1 + e^2)),
@@ -422,12 +423,12 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         const float a6 = fmaf(6.f, e2, 1.f), a3 = 3.f * (1.f + e2);
         const float iq = 1.f / (a6 * a3);
         const float ux = a3 * iq;
-        const float yk = fmaf(6.f * e2, e, 1.f) * (a6 * iq) * (float)(P.u_nphi - 1);
-        float fxu = fminf(fmaxf(ux * (P.u_ne - 1), 0.f), (float)(P.u_ne - 1));
+        const float yk = fmaf(6.f * e2, e, 1.f) * (a6 * iq) * P.u_nphi1f;
+        float fxu = fminf(fmaxf(ux * P.u_ne1f, 0.f), P.u_ne1f);
         int ui0 = (int)fxu, ui1 = min(ui0 + 1, P.u_ne - 1);
         float utx = fxu - ui0;
         auto ulook = [&](float ph) {
-          float fy = fminf(fmaxf(ph * yk, 0.f), (float)(P.u_nphi - 1));
+          float fy = fminf(fmaxf(ph * yk, 0.f), P.u_nphi1f);
           int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
           float ty2 = fy - j0;
           if (!check(j0 >= 0 && j1 < P.u_nphi && ui0 >= 0 && ui1 < P.u_ne)) return 0.f;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(256, BH_RENDER_MIN_BLOCKS) render_kernel(const
         float tcam = 0.f, tapsis = 0.f;
         auto t_of_R = [](float R, float uu) { return R - 1.f / uu + logf(uu / (1.f - uu)); };
         auto ulookT = [&](float ph) {
-          float fy = fminf(fmaxf(ph * yk, 0.f), (float)(P.u_nphi - 1));
+          float fy = fminf(fmaxf(ph * yk, 0.f), P.u_nphi1f);
           int j0 = (int)fy, j1 = min(j0 + 1, P.u_nphi - 1);
           float ty2 = fy - j0;
           if (!check(j0 >= 0 && j1 < P.u_nphi && ui0 >= 0 && ui1 < P.u_ne)) return 0.f;
@@ -1020,6 +1021,9 @@ static bh_status fill_params(bh_ctx *ctx, const bh_tables *t, const bh_cubemap *
   P.U = t->U;
   P.u_ne = t->desc.u_ne;
   P.u_nphi = t->desc.u_nphi;
+  P.d_n1f = (float)(t->desc.d_n - 1);
+  P.u_ne1f = (float)(t->desc.u_ne - 1);
+  P.u_nphi1f = (float)(t->desc.u_nphi - 1);
   size_t es = t->desc.storage == BH_F32 ? 4 : 2;
   P.u_bytes = (int)(((size_t)P.u_ne * P.u_nphi * es + 15) / 16 * 16);
   P.DTt = t->DT;
