@@ -578,6 +578,9 @@ def run_ours(args):
     e2e["rgb_async"] = ws * e2e_steps / (time.perf_counter() - t)
     del hosts
     e2e_fps = e2e["rgb_async"]
+    # the link's own bandwidth (the library's measurement, the frame's size)
+    link = bh.bh_measure_host_link(local, W * H * 12)
+    link_gbs = max(link["copy_engine_gbs"], link["kernel_stores_gbs"])
 
     # --- plain and served forms on equal terms: host wall clock per frame,
     # 2000 frames each, the same cameras, no L2 flush on either side
@@ -656,7 +659,12 @@ def run_ours(args):
                 "d2h_bytes_per_step": W * H * 12, "frames": e2e_steps,
                 "api": "bh_render_to_host_async + bh_host_wait (packed linear RGB into pinned host memory, "
                        "two frames in flight: one renders while the other is copied)",
-                "one_at_a_time_frames_per_s": e2e["rgb"], "rgba_one_at_a_time_frames_per_s": e2e["rgba"]},
+                "one_at_a_time_frames_per_s": e2e["rgb"], "rgba_one_at_a_time_frames_per_s": e2e["rgba"],
+                "host_link": {"copy_engine_gbs": link["copy_engine_gbs"],
+                              "kernel_stores_gbs": link["kernel_stores_gbs"],
+                              "achieved_gbs": e2e_fps * W * H * 12 / 1e9,
+                              "frac": e2e_fps * W * H * 12 / 1e9 / link_gbs,
+                              "note": "bh_measure_host_link on this box: the frame's bytes device -> pinned host"}},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed_region": wall,

@@ -98,6 +98,16 @@ bh_status bh_inject_fault(bh_ctx *ctx, int kind);
  * out holds 5 doubles.  Synchronises the device; allocates a few bytes. */
 bh_status bh_measure_issue_rates(int device, double *out);
 
+/* Bandwidth from device memory to pinned host memory on CUDA device
+ * `device`, the bound of every frame that goes to the host: `bytes` (rounded
+ * down to a multiple of 16, at least 16) moved by the copy engine
+ * (cudaMemcpyAsync device to pinned host, out[0]) and written into mapped
+ * pinned host memory by the library's own kernel stores (whole 128-byte lines
+ * per warp, out[1]), each in GB/s, the best of five timed runs after one
+ * untimed.  Allocates `bytes` of device memory and of pinned host memory for
+ * the call; synchronous.  BH_ERR_INVALID_ARG for a NULL out or bytes < 16. */
+bh_status bh_measure_host_link(int device, size_t bytes, double *out);
+
 /* ------------------------------------------------------------------------ */
 /* Tables D(e,u), U(e,phi) (Algorithm 1 PRECOMPUTE, Sec. 3.3.2-3.3.3,        */
 /* Appendix A) and the colour tables (Sec. 3.4.2)                             */

@@ -117,6 +117,7 @@ def lib():
             "bh_serve_flush": [_vp],
             "bh_check_status": [_vp, _vp],
             "bh_measure_issue_rates": [C.c_int, P(C.c_double)],
+            "bh_measure_host_link": [C.c_int, C.c_size_t, P(C.c_double)],
             "bh_bloom_weights": [C.c_double, C.c_int, C.c_int, P(C.c_double)],
             "bh_bloom": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, P(C.c_double), _vp],
             "bh_inject_fault": [_vp, C.c_int],
@@ -257,6 +258,13 @@ def bh_measure_issue_rates(device: int = 0) -> dict:
     _check(lib().bh_measure_issue_rates(device, o))
     return {"fp32_fma_per_sm_clk": o[0], "ffma2_fma_per_sm_clk": o[1], "mufu_per_sm_clk": o[2],
             "sms": int(o[3]), "sm_mhz": o[4]}
+
+
+def bh_measure_host_link(device: int = 0, nbytes: int = 1 << 25) -> dict:
+    """Device-to-pinned-host bandwidth (GB/s) by the copy engine and by kernel stores."""
+    o = (C.c_double * 2)()
+    _check(lib().bh_measure_host_link(device, nbytes, o))
+    return {"copy_engine_gbs": o[0], "kernel_stores_gbs": o[1], "bytes": nbytes}
 
 
 def bh_inject_fault(ctx: int, kind: int = BH_FAULT_TABLE_WAIT) -> None:

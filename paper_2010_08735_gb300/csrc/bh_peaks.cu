@@ -78,9 +78,64 @@ __global__ void __launch_bounds__(kPeakThreads) peak_mufu_kernel(int iters, floa
   if (s == 1234.5f) sink[threadIdx.x] = s;
 }
 
+// Zero-copy stores into mapped pinned host memory: every thread writes
+// 16-byte chunks, a warp 512 contiguous bytes per instruction (whole 128-byte
+// lines), grid-stride.
+__global__ void link_store_kernel(float4 *dst, long long n4) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = make_float4((float)(i & 1023), 1.f, 2.f, 3.f);
+}
+
 }  // namespace bh
 
 using namespace bh;
+
+// Bandwidth of the link from the device to host memory, for the end-to-end
+// (frames to the host) roofline: bytes (rounded down to 16) moved from device
+// memory to pinned host memory by the copy engine, and written into pinned
+// host memory by kernel stores; best of five timed runs each after one
+// untimed.
+extern "C" bh_status bh_measure_host_link(int device, size_t bytes, double *out) {
+  if (!out || bytes < 16) { set_error("bh_measure_host_link: NULL out or fewer than 16 bytes"); return BH_ERR_INVALID_ARG; }
+  bytes &= ~(size_t)15;
+  BH_CUDA(cudaSetDevice(device));
+  int sms = 0;
+  BH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  void *dev = nullptr, *host = nullptr, *mapped = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&dev, bytes);
+  if (e == cudaSuccess) e = cudaHostAlloc(&host, bytes, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&mapped, host, 0);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, bytes, s);
+  double gbs[2] = {0.0, 0.0};
+  for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, s);
+      if (which == 0) e = cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s);
+      else link_store_kernel<<<sms * 4, 256, 0, s>>>(static_cast<float4 *>(mapped), (long long)(bytes / 16));
+      if (e == cudaSuccess) e = cudaGetLastError();
+      cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && rep > 0 && ms > 0.f) gbs[which] = std::max(gbs[which], bytes / (ms * 1e-3) / 1e9);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (host) cudaFreeHost(host);
+  if (dev) cudaFree(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "bh_measure_host_link");
+  out[0] = gbs[0];
+  out[1] = gbs[1];
+  return BH_OK;
+}
 
 extern "C" bh_status bh_measure_issue_rates(int device, double *out) {
   if (!out) { set_error("bh_measure_issue_rates: NULL argument"); return BH_ERR_INVALID_ARG; }

@@ -572,6 +572,16 @@ def test_render_to_host_rgb_equals_device(ctx, gpu_tables, static_scene, W, H):
     assert np.array_equal(pageable, ref)
 
 
+def test_host_link_measurement():
+    """The device-to-host bandwidth measurement returns plausible rates for
+    both paths and rejects sizes below one 16-byte chunk."""
+    r = bh.bh_measure_host_link(0, 1 << 24)
+    for k in ("copy_engine_gbs", "kernel_stores_gbs"):
+        assert 1.0 < r[k] < 5000.0, r
+    with pytest.raises(bh.BhError):
+        bh.bh_measure_host_link(0, 8)
+
+
 def test_render_to_host_async_frames_in_flight(ctx, gpu_tables, static_scene):
     """Two frames in flight: a sequence of frames of changing camera, sizes and
     both layouts, each enqueued before the previous one is waited for, lands
