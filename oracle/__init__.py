@@ -11,10 +11,12 @@ ctypes and numpy.  Each wrapped function names the passage of the paper it
 follows (E. Bruneton, "Real-time High-Quality Rendering of Non-Rotating Black
 Holes", 2020).
 
-Parity unpinned: the colour observer and the C(xy, D) spectrum choice
-(``colour_table``, ``disc_colour_table``, ``blackbody_xyz``) are project
-definitions; only their internal consistency (black-body temperature shift,
-Planck integration) is pinned, not absolute colorimetry.
+Colour: the observer (piecewise-Gaussian colour-matching functions) is pinned
+in absolute terms through ``blackbody_xyz``, whose chromaticities lie on the
+published Planckian locus within the fit's accuracy; the C(xy, D)
+chromaticity-to-spectrum choice (``colour_table``, the paper's A1 = A2 = 0) is
+a project definition whose internal consistency (black-body temperature shift)
+is pinned -- parity unpinned for that choice itself.
 """
 from __future__ import annotations
 

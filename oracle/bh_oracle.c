@@ -39,8 +39,9 @@
  * intermediate textures).
  *
  * Parity notes: the colour observer (piecewise-Gaussian colour matching
- * functions) and the C(xy,D) chromaticity-to-spectrum choice are project
- * definitions, "parity unpinned" for absolute colorimetry.
+ * functions) is pinned to the published Planckian locus through the black
+ * body's chromaticity; the C(xy,D) chromaticity-to-spectrum choice is a
+ * project definition, "parity unpinned" for that choice itself.
  */
 #include <math.h>
 #include <pthread.h>

@@ -337,6 +337,67 @@ def test_blackbody_xyz_integral(orc):
             assert tr[c] == pytest.approx(ref, rel=2e-3)
 
 
+def kim_planckian_locus(T):
+    """CIE 1931 chromaticity of a black body at T kelvin (1667-25000 K) from the
+    published cubic-spline fit of the Planckian locus of Kim, Lee, Kim et al.,
+    "Design of advanced color temperature control system for HDTV
+    applications", J. Korean Phys. Soc. 41 (2002) -- independent of the
+    oracle's colour-matching functions and spectral integration."""
+    if T <= 4000.0:
+        x = -0.2661239e9 / T ** 3 - 0.2343589e6 / T ** 2 + 0.8776956e3 / T + 0.179910
+    else:
+        x = -3.0258469e9 / T ** 3 + 2.1070379e6 / T ** 2 + 0.2226347e3 / T + 0.240390
+    if T <= 2222.0:
+        y = -1.1063814 * x ** 3 - 1.34811020 * x ** 2 + 2.18555832 * x - 0.20219683
+    elif T <= 4000.0:
+        y = -0.9549476 * x ** 3 - 1.37418593 * x ** 2 + 2.09137015 * x - 0.16748867
+    else:
+        y = 3.0817580 * x ** 3 - 5.87338670 * x ** 2 + 3.75112997 * x - 0.37001483
+    return x, y
+
+
+# oracle black body vs the published locus: the project's piecewise-Gaussian
+# observer is an approximation of CIE 1931, least exact in the deep red
+LOCUS_TOL = [(2600.0, 4e-3), (4500.0, 1.5e-3), (25000.0, 5e-4)]
+
+
+def locus_tolerance(T):
+    return next(tol for top, tol in LOCUS_TOL if T <= top)
+
+
+def test_blackbody_chromaticity_on_published_planckian_locus(orc):
+    """Absolute colorimetry (reading C14): the chromaticity of the oracle's
+    black body, XYZ(B_T) through its colour-matching functions, lies on the
+    published Planckian locus from 1700 K to 25000 K within the accuracy of a
+    Gaussian-lobe fit of the CIE observer.  The pin discriminates: the same
+    integration with the second radiation constant 2 % off misses the locus."""
+    temps = [1700, 2000, 2500, 3000, 3500, 4000, 5000, 6500, 8000, 10000, 15000, 20000, 25000]
+
+    def xy(xyz):
+        return xyz[0] / xyz.sum(), xyz[1] / xyz.sum()
+
+    for T in temps:
+        x, y = xy(orc.blackbody_xyz(T))
+        kx, ky = kim_planckian_locus(T)
+        tol = locus_tolerance(T)
+        assert abs(x - kx) <= tol and abs(y - ky) <= tol, (T, x, y, kx, ky)
+    # planted mistake: the oracle's spectral sum redone here with c2 2 % high
+    lam = 360.0 + 5.0 * np.arange(95)
+    w = np.full(lam.shape, 5.0)
+    w[0] = w[-1] = 2.5
+    cmf = np.array([orc.cmf(float(l)) for l in lam])
+
+    def planted_xy(T, c2):
+        b = w / (lam ** 5 * np.expm1(c2 / (lam * T)))
+        return xy(b @ cmf)
+
+    for T in (3000, 6500):  # the re-done sum reproduces the oracle with the true constant
+        assert np.allclose(planted_xy(T, 1.4387769e7), xy(orc.blackbody_xyz(T)), rtol=0, atol=1e-12)
+    off = [max(abs(a - b) for a, b in zip(planted_xy(T, 1.02 * 1.4387769e7), kim_planckian_locus(T)))
+           > locus_tolerance(T) for T in temps]
+    assert any(off)
+
+
 def test_blackbody_xyz_positive_and_ordered(orc):
     """Hotter black bodies are bluer: z/(x+y+z) grows with T."""
     zs = []
